@@ -1,0 +1,126 @@
+"""CPU oracle for the energy-game initial credit problem (arXiv 1710.03647).
+
+TEST INFRASTRUCTURE ONLY: tests, the smoke check and the benchmark's CPU
+baseline may use this package; the CUDA product path never does.  It shares
+no code with the CUDA solver.  `oracle.c` holds the arithmetic:
+
+  bound(...)        M_G of Sec. 3.1
+  solve(...)        Algorithm 1 of Sec. 3.1 (FIFO worklist with counters)
+  brute_force(...)  Lemma "EGcycles" by strategy enumeration + Bellman-Ford
+  check(...)        least-EPM equations of Def. "EPM" / "Lifting Operator"
+
+Credits are int64 numpy arrays with TOP = INT64_MAX.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+TOP = np.iinfo(np.int64).max
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into a shared library with the host C compiler."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        os.makedirs(_LIB_DIR, exist_ok=True)
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        i64, p = ctypes.c_int64, ctypes.c_void_p
+        lib.oracle_bound.restype = i64
+        lib.oracle_bound.argtypes = [i64, p, p]
+        lib.oracle_solve.restype = ctypes.c_int
+        lib.oracle_solve.argtypes = [i64, p, p, p, p, i64, i64, p, p]
+        lib.oracle_brute_force.restype = ctypes.c_int
+        lib.oracle_brute_force.argtypes = [i64, p, p, p, p, i64, p]
+        lib.oracle_check.restype = ctypes.c_int
+        lib.oracle_check.argtypes = [i64, p, p, p, p, i64, p, p]
+        _lib = lib
+    return _lib
+
+
+def _arrays(row_ptr, col, w, owner_bits):
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    w = np.ascontiguousarray(w, dtype=np.int64)
+    owner_bits = np.ascontiguousarray(owner_bits, dtype=np.uint32)
+    if owner_bits.size == 0:
+        owner_bits = np.zeros(1, dtype=np.uint32)
+    return row_ptr, col, w, owner_bits
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def bound(n: int, row_ptr, w) -> int:
+    """M_G = sum_v max(0, max over out-edges of -w)."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    w = np.ascontiguousarray(w, dtype=np.int64)
+    return int(_load().oracle_bound(n, _ptr(row_ptr), _ptr(w) if w.size else None))
+
+
+def solve(n: int, row_ptr, col, w, owner_bits, C: int | None = None, max_lifts: int = 0):
+    """Algorithm 1.  Returns (f int64[n] with TOP, stats dict)."""
+    row_ptr, col, w, owner_bits = _arrays(row_ptr, col, w, owner_bits)
+    if C is None:
+        C = bound(n, row_ptr, w)
+    f = np.zeros(max(n, 1), dtype=np.int64)
+    st = np.zeros(4, dtype=np.int64)
+    rc = _load().oracle_solve(n, _ptr(row_ptr), _ptr(col), _ptr(w), _ptr(owner_bits), C, max_lifts,
+                              _ptr(f), _ptr(st))
+    if rc == 1:
+        raise OracleError("arena is not total: a vertex has no successor")
+    if rc == 2:
+        raise OracleError(f"lift budget of {max_lifts} exhausted")
+    if rc != 0:
+        raise OracleError(f"oracle_solve failed with {rc}")
+    stats = dict(C=C, lifts=int(st[0]), lift_edge_evals=int(st[1]), pre_scans=int(st[2]),
+                 recount_evals=int(st[3]))
+    return f[:n], stats
+
+
+def brute_force(n: int, row_ptr, col, w, owner_bits, max_strategies: int = 1 << 20):
+    """Minimum credits by exhaustive strategy enumeration (tiny arenas only)."""
+    row_ptr, col, w, owner_bits = _arrays(row_ptr, col, w, owner_bits)
+    c = np.zeros(max(n, 1), dtype=np.int64)
+    rc = _load().oracle_brute_force(n, _ptr(row_ptr), _ptr(col), _ptr(w), _ptr(owner_bits),
+                                    max_strategies, _ptr(c))
+    if rc == 1:
+        raise OracleError("arena is not total: a vertex has no successor")
+    if rc == 2:
+        raise OracleError("too many strategies for brute force")
+    if rc != 0:
+        raise OracleError(f"oracle_brute_force failed with {rc}")
+    return c[:n]
+
+
+def check(n: int, row_ptr, col, w, owner_bits, f, C: int | None = None):
+    """(code, vertex): 0 if f is a fixpoint of every lift within {0..C} u {TOP}."""
+    row_ptr, col, w, owner_bits = _arrays(row_ptr, col, w, owner_bits)
+    if C is None:
+        C = bound(n, row_ptr, w)
+    f = np.ascontiguousarray(f, dtype=np.int64)
+    bad = np.zeros(1, dtype=np.int64)
+    rc = _load().oracle_check(n, _ptr(row_ptr), _ptr(col), _ptr(w), _ptr(owner_bits), C, _ptr(f),
+                              _ptr(bad))
+    return int(rc), int(bad[0])

@@ -1,0 +1,191 @@
+"""Pins for the CPU oracle (Algorithm 1 of arXiv 1710.03647, Sec. 3.1).
+
+The oracle is checked against things other than itself:
+  * hand-worked games derived from Eq. 1 / Def. "EPM" (tests/golden),
+  * closed forms of Eq. 1 for single-successor arenas (lassos and cycles),
+  * brute force over player-0 memoryless strategies (Lemma "EGcycles") on
+    thousands of random tiny arenas,
+  * the least-EPM equations and the bound M_G on larger arenas,
+  * planted mistakes (mutants of oracle.c compiled here) that these pins
+    must catch.
+"""
+from __future__ import annotations
+
+import os
+import re
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1710_03647_gb300 import gen
+from tests._games import TOP64, arena_from_edges, functional_credit, load_hand_games
+
+
+def solve(a, **kw):
+    f, st = oracle.solve(a.n, a.row_ptr, a.col, a.w, a.owner_bits, **kw)
+    return f, st
+
+
+@pytest.mark.parametrize("game", load_hand_games(), ids=lambda g: g[0].name)
+def test_hand_games(game):
+    a, bound, expect = game
+    assert oracle.bound(a.n, a.row_ptr, a.w) == bound
+    f, _ = solve(a)
+    np.testing.assert_array_equal(f, expect)
+    # the hand-worked answers also agree with the exhaustive definition
+    np.testing.assert_array_equal(oracle.brute_force(a.n, a.row_ptr, a.col, a.w, a.owner_bits), expect)
+    assert oracle.check(a.n, a.row_ptr, a.col, a.w, a.owner_bits, f)[0] == 0
+
+
+def test_bound_by_hand():
+    # M_G = sum_v max(0, max_e -w): rows {-3, 5}, {2}, {-7, -1, 0}
+    a = arena_from_edges([0, 1, 0], [(0, 1, -3), (0, 2, 5), (1, 0, 2), (2, 0, -7), (2, 1, -1), (2, 2, 0)])
+    assert oracle.bound(a.n, a.row_ptr, a.w) == 3 + 0 + 7
+
+
+@pytest.mark.parametrize("seed", range(200))
+def test_single_successor_closed_form(seed):
+    s = gen.Stream(seed, 99)
+    n = int(1 + s.below(1, 12)[0])
+    succ = gen.Stream(seed, 98).below(n, n)
+    weight = gen.Stream(seed, 97).integers(n, -6, 6)
+    owners = gen.Stream(seed, 96).below(n, 2).astype(bool)
+    a = arena_from_edges(owners, [(v, int(succ[v]), int(weight[v])) for v in range(n)])
+    f, _ = solve(a)
+    np.testing.assert_array_equal(f, functional_credit(succ, weight))
+
+
+def _tiny(seed):
+    s = gen.Stream(seed, 90)
+    n = int(1 + s.below(1, 7)[0])
+    p1 = float(gen.Stream(seed, 91).unit(1)[0])
+    return gen.tiny_game(n, max_deg=3, wlo=-4, whi=4, seed=seed, p1=p1)
+
+
+@pytest.mark.parametrize("block", range(10))
+def test_brute_force_random_tiny(block):
+    for seed in range(block * 300, (block + 1) * 300):
+        a = _tiny(seed)
+        f, _ = solve(a)
+        bf = oracle.brute_force(a.n, a.row_ptr, a.col, a.w, a.owner_bits)
+        assert np.array_equal(f, bf), (seed, f, bf)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_brute_force_one_player(seed):
+    # all player 1: a single strategy, the textbook worst-case walk
+    a = gen.tiny_game(int(5 + seed % 20), max_deg=3, wlo=-5, whi=5, seed=1000 + seed, p1=1.0)
+    f, _ = solve(a)
+    np.testing.assert_array_equal(f, oracle.brute_force(a.n, a.row_ptr, a.col, a.w, a.owner_bits))
+
+
+@pytest.mark.parametrize("seed", range(1, 6))
+def test_uniform_1k_invariants(seed):
+    a = gen.config(1, seed)
+    C = oracle.bound(a.n, a.row_ptr, a.w)
+    f, st = solve(a)
+    assert oracle.check(a.n, a.row_ptr, a.col, a.w, a.owner_bits, f, C)[0] == 0
+    fin = f[f != TOP64]
+    assert fin.size and fin.max() <= C and fin.min() >= 0
+    assert 0 < (f == TOP64).sum() < a.n
+    assert st["lifts"] > 0
+
+
+def test_equation_check_rejects_wrong_answers():
+    a = gen.config(1, 1)
+    f, _ = solve(a)
+    fin = np.nonzero(f != TOP64)[0]
+    g = f.copy()
+    g[fin[0]] += 1
+    assert oracle.check(a.n, a.row_ptr, a.col, a.w, a.owner_bits, g)[0] == 2
+    g = f.copy()
+    g[fin[0]] = -1
+    assert oracle.check(a.n, a.row_ptr, a.col, a.w, a.owner_bits, g)[0] == 1
+
+
+def test_non_total_rejected():
+    a = arena_from_edges([0, 1], [(0, 1, 1)])  # vertex 1 has no successor
+    with pytest.raises(oracle.OracleError):
+        solve(a)
+
+
+def test_solution_independent_of_cap_above_credits():
+    # Any cap at or above the largest finite credit gives the same least
+    # fixpoint (the bounded operator only turns values above the cap into TOP).
+    a = gen.config(1, 2)
+    f, _ = solve(a)
+    C = oracle.bound(a.n, a.row_ptr, a.w)
+    g, _ = solve(a, C=2 * C)
+    np.testing.assert_array_equal(f, g)
+
+
+# ---- planted mistakes: each mutant of oracle.c must fail some pin ----------
+
+MUTANTS = {
+    "minus_sign": (r"int64_t d = a - b;", "int64_t d = a + b;"),
+    "cap_off_by_one": (r"if \(d > C\)\n        return ORACLE_TOP;", "if (d >= C)\n        return ORACLE_TOP;"),
+    "min_max_swapped": (r"if \(p1 \? \(t > g\) : \(t < g\)\)", "if (p1 ? (t < g) : (t > g))"),
+    "counter_strict": (r"if \(count\[u\] <= 0\)", "if (count[u] < 0)"),
+    "init_p1_needs_all_negative": (r"if \(is_p1\(owner_bits, v\) \? any_neg : all_neg\)", "if (all_neg)"),
+    "pre_filter_flipped": (r"if \(!\(f\[u\] < ominus\(f\[v\], wu, C\)\)\)", "if (!(f[u] > ominus(f[v], wu, C)))"),
+}
+
+
+def _mutant_lib(tmpdir, name):
+    pat, rep = MUTANTS[name]
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "oracle.c")).read()
+    mutated, k = re.subn(pat, rep, src)
+    assert k >= 1, f"mutation {name} did not apply"
+    c = os.path.join(tmpdir, f"{name}.c")
+    so = os.path.join(tmpdir, f"{name}.so")
+    open(c, "w").write(mutated)
+    subprocess.check_call(["gcc", "-O1", "-std=c99", "-shared", "-fPIC", "-o", so, c])
+    return so
+
+
+def _pins_pass(lib_path) -> bool:
+    """Runs the hand games and a brute-force sample through a given library."""
+    import ctypes
+
+    lib = ctypes.CDLL(lib_path)
+    i64, p = ctypes.c_int64, ctypes.c_void_p
+    lib.oracle_solve.restype = ctypes.c_int
+    lib.oracle_solve.argtypes = [i64, p, p, p, p, i64, i64, p, p]
+    lib.oracle_bound.restype = i64
+    lib.oracle_bound.argtypes = [i64, p, p]
+
+    def run(a):
+        rp = np.ascontiguousarray(a.row_ptr, dtype=np.int64)
+        col = np.ascontiguousarray(a.col, dtype=np.int32)
+        w = np.ascontiguousarray(a.w, dtype=np.int64)
+        ob = np.ascontiguousarray(a.owner_bits, dtype=np.uint32)
+        C = lib.oracle_bound(a.n, rp.ctypes.data, w.ctypes.data)
+        f = np.zeros(a.n, dtype=np.int64)
+        st = np.zeros(4, dtype=np.int64)
+        rc = lib.oracle_solve(a.n, rp.ctypes.data, col.ctypes.data, w.ctypes.data, ob.ctypes.data, C,
+                              10_000_000, f.ctypes.data, st.ctypes.data)
+        return rc, f
+
+    for a, _, expect in load_hand_games():
+        rc, f = run(a)
+        if rc != 0 or not np.array_equal(f, expect):
+            return False
+    for seed in range(400):
+        a = _tiny(seed)
+        rc, f = run(a)
+        if rc != 0 or not np.array_equal(f, oracle.brute_force(a.n, a.row_ptr, a.col, a.w, a.owner_bits)):
+            return False
+    return True
+
+
+def test_pins_pass_on_real_oracle():
+    assert _pins_pass(oracle.build())
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name):
+    with tempfile.TemporaryDirectory() as d:
+        assert not _pins_pass(_mutant_lib(d, name)), f"mutant {name} slipped through the pins"
