@@ -1,0 +1,297 @@
+#!/usr/bin/env python3
+"""Benchmark: least-fixpoint lifting of the energy progress measure on one
+R-MAT energy game (2^20 vertices, ~8.8M edges, weights in [-100, 100],
+int32 credits), solved to the fixpoint per step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Metric: edge-relaxations/s, i.e. evaluations
+of f(u) (-) w over edges (pulls of player-0 lifts plus pushes to
+predecessors) divided by the device time of the solve; time-to-fixpoint per
+step is ms_per_step.  The arena is resident in HBM before the timed region;
+between timed steps a 512 MiB buffer is rewritten to flush L2.
+
+--impl reference times the CPU oracle (Algorithm 1, single thread) on a
+bounded sample: the same generator at 2^16 vertices per step.
+
+A single game does not shard: with --gpus N every rank solves its own
+replica (no collective on the data path) and value sums the ranks' work
+over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(workload="rmat20_s1: R-MAT scale 20 (a,b,c,d)=(.57,.19,.19,.05), 8*2^20 draws, "
+                         "w uniform in [-100,100], owner Bernoulli(0.5), seed 1",
+                scale=20, seed=1, credit_bits=32)
+METRIC = "edge-relaxations/s"
+UNIT = "relax/s"
+# algorithmic bytes (per unit): relaxation = index 4 + weight 4 + credit s;
+# list entry (lift or push) = two offsets 8 + entry 4 + credit s;
+# enqueue = entry write 4 + bitmap word 4
+def algorithmic_bytes(st, s):
+    return st["relaxations"] * (8 + s) + (st["lifts"] + st["pushes"]) * (12 + s) + st["enqueues"] * 8
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    from paper_1710_03647_gb300 import gen
+
+    sample_scale = 16
+    a = gen.rmat_game(sample_scale, 8, seed=WORKLOAD["seed"])
+    C = oracle.bound(a.n, a.row_ptr, a.w)
+    times, relax = [], []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        _, st = oracle.solve(a.n, a.row_ptr, a.col, a.w, a.owner_bits, C)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            relax.append(st["lift_edge_evals"] + st["pre_scans"] + st["recount_evals"])
+    value = sum(relax) / sum(times)
+    sample = (f"oracle (Algorithm 1, 1 thread) on R-MAT scale {sample_scale} (n={a.n}, m={a.m}), "
+              f"same generator and seed, one full solve per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic", "config": {"workload": WORKLOAD["workload"], "sample_scale": sample_scale},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def cpu_baseline():
+    """The oracle as it stands, single-threaded, on a bounded sample (~10-30 s)."""
+    import oracle
+    from paper_1710_03647_gb300 import gen
+
+    scale = 16
+    a = gen.rmat_game(scale, 8, seed=WORKLOAD["seed"])
+    t0 = time.perf_counter()
+    _, st = oracle.solve(a.n, a.row_ptr, a.col, a.w, a.owner_bits)
+    dt = time.perf_counter() - t0
+    relax = st["lift_edge_evals"] + st["pre_scans"] + st["recount_evals"]
+    return {"value": relax / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"R-MAT scale {scale} (n={a.n}, m={a.m}) from the same generator, one full solve "
+                      f"({dt:.1f} s, {relax} edge evaluations)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+        pg = dist
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1710_03647_gb300 import eg, gen
+
+    a = gen.rmat_game(WORKLOAD["scale"], 8, seed=WORKLOAD["seed"])
+    bits = WORKLOAD["credit_bits"]
+    s = bits // 8
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    out = torch.empty(a.n, dtype=torch.int32 if bits == 32 else torch.int64, device=dev)
+    arena = eg.Arena(a)
+
+    def step():
+        _, st = eg.eg_solve_credit(arena.handle, bits, 1, 0, out, stream=stream.cuda_stream)
+        return st
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xff)  # rewrite > L2 between steps (untimed)
+                ev[k][0].record(stream)
+            st = step()
+            ev[k][1].record(stream)
+            stats.append(st.as_dict())
+        torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    step_ms = [b.elapsed_time(e) for b, e in ev]
+    total_ms = sum(step_ms)
+    relax = sum(x["relaxations"] for x in stats)
+    launches = 2 * args.steps  # init + persistent fixpoint per step
+    if pg:
+        t = torch.tensor([total_ms, relax], dtype=torch.float64, device=dev)
+        tmax = t.clone()
+        pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
+        pg.all_reduce(t, op=pg.ReduceOp.SUM)
+        total_ms_max, relax_all = float(tmax[0]), float(t[1])
+    else:
+        total_ms_max, relax_all = total_ms, float(relax)
+
+    # dominant kernel: the persistent fixpoint; its duration from CUDA events
+    # recorded around its launch on this stream
+    fix_ms = sum(x["fixpoint_ms"] for x in stats)
+    bytes_alg = sum(algorithmic_bytes(x, s) for x in stats)
+    peak, peak_kind = peaks()
+    achieved = bytes_alg / (fix_ms * 1e-3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "fixpoint_rmat20_traffic.json")
+    if os.path.exists(prof):
+        traffic = json.load(open(prof)).get("dram_bytes_per_launch")
+
+    # end to end through the public API: host arrays in, host credits out
+    e2e = None
+    if rank == 0:
+        host_out = np.empty(a.n, dtype=np.int32 if bits == 32 else np.int64)
+        rp = np.ascontiguousarray(a.row_ptr)
+        e_times, e_relax = [], 0
+        for k in range(max(2, args.steps // 2)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = eg.eg_create(a.n, a.m, rp, a.col, a.w, owner_bits=a.owner_bits)
+            _, st = eg.eg_solve_credit(h, bits, 1, 0, host_out)
+            eg.eg_destroy(h)
+            e_times.append(time.perf_counter() - t0)
+            e_relax += st.relaxations
+        h2d = rp.nbytes + a.col.nbytes + a.w.nbytes + a.owner_bits.nbytes
+        e2e = {"value": e_relax / sum(e_times), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(host_out.nbytes + 128),
+               "ms_per_step": 1e3 * sum(e_times) / len(e_times)}
+
+    if rank != 0:
+        arena.close()
+        if pg:
+            pg.destroy_process_group()
+        return
+    golden = os.path.join(ROOT, "tests", "golden", "rmat20_s1.json")
+    oracle_relax = None
+    if os.path.exists(golden):
+        g = json.load(open(golden))
+        oracle_relax = g["oracle_lift_edge_evals"] + g["oracle_pre_scans"]
+    cpu = None if args.no_cpu_baseline else cpu_baseline()
+    st0 = stats[-1]
+    line = {
+        "metric": METRIC, "value": relax_all / (total_ms_max * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32" if bits == 32 else "int64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD["workload"], "n": a.n, "m": a.m, "credit_bits": bits,
+                   "parallelism": "replicas" if world > 1 else "single", "l2": "flushed between steps (512 MiB write)"},
+        "time_to_fixpoint_ms": statistics.median(step_ms),
+        "rounds": st0["rounds"], "relaxations_per_step": st0["relaxations"], "lifts": st0["lifts"],
+        "pushes": st0["pushes"], "oracle_relaxations": oracle_relax,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "kernel": "k_fixpoint", "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": bytes_alg / args.steps,
+                     "kernel_ms_per_launch": fix_ms / args.steps},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    arena.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

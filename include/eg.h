@@ -1,0 +1,142 @@
+/*
+ * eg.h -- C ABI of the GB300 energy-game solver.
+ *
+ * Problem (arXiv 1710.03647, Sec. 3, Def. "Initial Credit Problem"): for a
+ * total weighted game arena G = (V, E, w, <V0, V1>) (Sec. 2), decide for every
+ * vertex v whether player 0 wins the energy objective (Eq. 1) and, if so,
+ * the minimum initial credit c(v).  The solver computes the least energy
+ * progress measure (Def. "EPM", Sec. 3.1) as the least fixpoint of the
+ * lifting operator (Def. "Lifting Operator") with the bounded operator
+ * a (-) b = TOP if a = TOP or a - b > C, else max(0, a - b), where C = M_G,
+ * the bound of Sec. 3.1.  TOP marks the vertices player 1 wins.
+ *
+ * Conventions for every call:
+ *   - No exception or C++ type crosses this boundary; every call returns an
+ *     eg_status, and on failure eg_last_error() gives a message for the
+ *     calling thread.
+ *   - Vertex ids are 0..n-1 in the caller's order; results use that order.
+ *   - Ownership is a bitmap of ceil(n/32) uint32 words: bit (v % 32) of word
+ *     v / 32 is 1 iff v is a player-1 vertex (V1), 0 iff player 0 (V0).
+ *   - Weights are int32.  A solve may view them through the integer map
+ *     w' = w_scale * w - w_shift (a mean-payoff threshold query, Sec. 3 on
+ *     the reduction between energy and mean-payoff games); the map is
+ *     applied on the fly, the arena is not rewritten.
+ *   - Host pointers are plain host memory; "device" pointers are CUDA device
+ *     memory of the current device.
+ */
+#ifndef EG_H
+#define EG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t eg_status;
+#define EG_OK 0
+#define EG_PENDING 1           /* eg_poll: request not finished yet */
+#define EG_ERR_INVALID (-1)    /* malformed arguments or CSR arrays */
+#define EG_ERR_NOT_TOTAL (-2)  /* a vertex has no successor (Sec. 2 assumes totality) */
+#define EG_ERR_OVERFLOW (-3)   /* int32 credits asked for but C + max|w'| does not fit */
+#define EG_ERR_OOM (-4)        /* device or host allocation failed */
+#define EG_ERR_CUDA (-5)       /* a CUDA runtime call failed */
+#define EG_ERR_TIMEOUT (-6)    /* a device-side wait ran past its spin limit */
+#define EG_ERR_BUDGET (-7)     /* the round budget ran out before the fixpoint */
+#define EG_ERR_BUSY (-8)       /* the server cannot take more requests now */
+
+#define EG_TOP32 INT32_MAX     /* TOP in int32 credit arrays */
+#define EG_TOP64 INT64_MAX     /* TOP in int64 credit arrays */
+
+/* eg_create flags */
+#define EG_INPUT_DEVICE 1u     /* the CSR/bitmap pointers are device pointers */
+
+typedef struct eg_arena eg_arena;
+typedef struct eg_server eg_server;
+
+/* Counters of one solve.  relaxations counts evaluations of f(u) (-) w over
+ * edges (pulls of player-0 lifts plus pushes to predecessors); lifts counts
+ * player-0 vertices lifted; pushes counts vertices whose rise was sent to
+ * their predecessors; rounds counts frontier rounds (Algorithm 3's loop). */
+typedef struct eg_stats {
+    int64_t C;             /* the bound M_G of the (mapped) weights */
+    int32_t credit_bits;   /* width the solve computed in: 32 or 64 */
+    int32_t status;        /* the solve's eg_status */
+    int64_t rounds;
+    int64_t lifts;
+    int64_t pushes;
+    int64_t relaxations;
+    int64_t enqueues;
+    double ms;             /* device time of initialisation + fixpoint kernels */
+    double fixpoint_ms;    /* device time of the persistent fixpoint kernel alone */
+} eg_stats;
+
+/*
+ * eg_create -- copy an arena to the device and build what the solver needs.
+ *
+ * Arena of Sec. 2: n vertices, m edges in forward CSR
+ *   row_ptr[n+1] (int64, row_ptr[0] = 0, non-decreasing, row_ptr[n] = m),
+ *   col[m] (int32 successor ids), w[m] (int32 weights w(v, col)).
+ * The predecessor sets pre(v) (Sec. 2) come as the reverse CSR
+ *   rrow_ptr[n+1], rcol[m] (predecessor ids), rw[m] (w of that edge),
+ * or all three NULL, in which case the library builds them on the device.
+ * A given reverse CSR must hold exactly the edges of the forward one (checked
+ * with a multiset hash; EG_ERR_INVALID otherwise).
+ * owner_bits: ceil(n/32) words as above.
+ *
+ * Requires 1 <= n < 2^31 and n <= m < 2^31.  Every vertex must have a
+ * successor (EG_ERR_NOT_TOTAL otherwise).  Duplicate edges and self-loops
+ * are allowed.  flags: EG_INPUT_DEVICE or 0 (host inputs).
+ *
+ * Ownership: the inputs stay the caller's and are not referenced after the
+ * call returns; the returned arena (and all device memory it holds) belongs
+ * to the library until eg_destroy.  Synchronous.
+ */
+eg_status eg_create(int64_t n, int64_t m,
+                    const int64_t *row_ptr, const int32_t *col, const int32_t *w,
+                    const int64_t *rrow_ptr, const int32_t *rcol, const int32_t *rw,
+                    const uint32_t *owner_bits, uint32_t flags, eg_arena **out);
+
+/* eg_destroy -- free an arena and its device memory.  NULL is accepted. */
+eg_status eg_destroy(eg_arena *arena);
+
+/*
+ * eg_bound -- the bound C = M_G (Sec. 3.1) of the arena under the map
+ * w' = w_scale * w - w_shift, and the largest |w'|; either output may be NULL.
+ */
+eg_status eg_bound(eg_arena *arena, int64_t w_scale, int64_t w_shift, int64_t *C, int64_t *max_abs_w);
+
+/*
+ * eg_solve_credit -- the least energy progress measure (Sec. 3.1), i.e. the
+ * minimum initial credits with TOP on the player-1 winning set.
+ *
+ * credit_bits: 32 -> credits_out is int32[n] (TOP = EG_TOP32), and the solve
+ *   fails with EG_ERR_OVERFLOW unless C + max|w'| <= INT32_MAX - 1;
+ *   64 -> credits_out is int64[n] (TOP = EG_TOP64), computed in int64;
+ *   0 -> credits_out is int64[n]; the solve computes in int32 when the rule
+ *   above allows it, else in int64.
+ * w_scale / w_shift: weight map as above (1 and 0 for the plain arena);
+ *   |w_scale| * 2^31 + |w_shift| must stay below 2^62.
+ * credits_out: host or device pointer (detected), caller-owned, n elements.
+ * st: optional counters (may be NULL).
+ * cuda_stream: the cudaStream_t to run on (NULL = the legacy default stream).
+ * max_rounds: round budget (0 = unlimited); EG_ERR_BUDGET when exceeded.
+ * Synchronous: returns after the credits are written.  One solve at a time
+ * per arena.  EG_ERR_TIMEOUT if a device-side wait gave up; the device
+ * stays usable and the arena can be solved again.
+ */
+eg_status eg_solve_credit(eg_arena *arena, int32_t credit_bits, int64_t w_scale, int64_t w_shift,
+                          void *credits_out, eg_stats *st, void *cuda_stream, int64_t max_rounds);
+
+/* eg_last_error -- message of the calling thread's last failure ("" if none). */
+const char *eg_last_error(void);
+
+/* eg_version -- library version string. */
+const char *eg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EG_H */

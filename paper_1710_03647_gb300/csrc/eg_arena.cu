@@ -1,0 +1,438 @@
+// Arena construction and the C ABI entry points of libeg.
+//
+// eg_create copies the forward CSR of the arena (Sec. 2) to the device,
+// validates it there (offsets, ids, totality), narrows the offsets to int32
+// and builds the predecessor sets pre(v) (Sec. 2) as a reverse CSR with the
+// owner of each predecessor in the high bit of its id: the paper's redundant
+// CSC representation (Sec. 5), built here by our own count / scan / scatter
+// kernels rather than a library transpose.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "eg_device.cuh"
+#include "eg_internal.h"
+
+namespace eg {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+void clear_error() { g_err[0] = 0; }
+
+enum : unsigned { BAD_ROWPTR = 1u, NOT_TOTAL = 2u, BAD_COL = 4u, BAD_RROWPTR = 8u, BAD_RCOL = 16u };
+
+// Validates the int64 forward offsets and narrows them to int32.
+__global__ void k_check_rows(const long long *rp64, int n, int m, int *rp32, unsigned *flags) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v <= n; v += gridDim.x * blockDim.x) {
+        long long a = rp64[v];
+        unsigned f = 0;
+        if (a < 0 || a > m) f |= BAD_ROWPTR;
+        if (v == 0 && a != 0) f |= BAD_ROWPTR;
+        if (v == n && a != m) f |= BAD_ROWPTR;
+        if (v < n) {
+            long long b = rp64[v + 1];
+            if (b < a) f |= BAD_ROWPTR;
+            else if (b == a) f |= NOT_TOTAL;
+        }
+        rp32[v] = (int)a;
+        if (f) atomicOr(flags, f);
+    }
+}
+
+__global__ void k_check_cols(const int *col, int m, int n, unsigned *flags, unsigned bad) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += gridDim.x * blockDim.x) {
+        unsigned c = (unsigned)col[e] & (bad == BAD_RCOL ? 0x7fffffffu : 0xffffffffu);
+        if (c >= (unsigned)n) atomicOr(flags, bad);
+    }
+}
+
+// in-degree counts into cnt[0..n-1] (cnt zeroed by the caller)
+__global__ void k_count_in(const int *col, int m, int *cnt) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += gridDim.x * blockDim.x)
+        atomicAdd(cnt + col[e], 1);
+}
+
+// Block-local exclusive scan of data[0..len) in place; block totals to sums.
+__global__ void k_scan_blocks(int *data, int len, int *sums) {
+    __shared__ int warp_tot[32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = i < len ? data[i] : 0;
+    int incl = x;
+    for (int d = 1; d < 32; d <<= 1) {
+        int o = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += o;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+        int ti = t;
+        for (int d = 1; d < 32; d <<= 1) {
+            int o = __shfl_up_sync(FULL, ti, d);
+            if (lane >= d) ti += o;
+        }
+        warp_tot[lane] = ti - t;
+        if (lane == 31 && sums) sums[blockIdx.x] = ti;
+    }
+    __syncthreads();
+    if (i < len) data[i] = incl - x + warp_tot[wid];
+}
+
+__global__ void k_add_offsets(int *data, int len, const int *offs) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) data[i] += offs[blockIdx.x];
+}
+
+// Exclusive scan of data[0..len) in place; scratch holds the block sums of
+// every level (at most len / 1024 + 64 ints).
+static cudaError_t exclusive_scan(int *data, int len, int *scratch, cudaStream_t s) {
+    const int B = 1024;
+    int nb = (len + B - 1) / B;
+    if (nb <= 1) {
+        k_scan_blocks<<<1, B, 0, s>>>(data, len, nullptr);
+        return cudaGetLastError();
+    }
+    k_scan_blocks<<<nb, B, 0, s>>>(data, len, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = exclusive_scan(scratch, nb, scratch + nb, s);
+    if (e != cudaSuccess) return e;
+    k_add_offsets<<<nb, B, 0, s>>>(data, len, scratch);
+    return cudaGetLastError();
+}
+
+// One warp per vertex scatters its out-edges into the reverse CSR.
+__global__ void k_scatter(int n, const int *row_ptr, const int *col, const int *w, const unsigned *owner_bits,
+                          int *fill, unsigned *rcol, int *rw) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n; v += nw) {
+        const unsigned tag = (unsigned)v | ((((owner_bits[v >> 5] >> (v & 31)) & 1u) != 0) ? P1_FLAG : 0u);
+        const int b = row_ptr[v], e = row_ptr[v + 1];
+        for (int k = b + lane; k < e; k += 32) {
+            const int u = col[k];
+            const int slot = atomicAdd(fill + u, 1);
+            rcol[slot] = tag;
+            rw[slot] = w[k];
+        }
+    }
+}
+
+// Tags caller-provided reverse columns with the owner bit of the predecessor.
+__global__ void k_tag_rcol(int m, const unsigned *owner_bits, unsigned *rcol) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += gridDim.x * blockDim.x) {
+        unsigned p = rcol[e] & 0x7fffffffu;
+        rcol[e] = p | ((((owner_bits[p >> 5] >> (p & 31)) & 1u) != 0) ? P1_FLAG : 0u);
+    }
+}
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ unsigned long long edge_hash(unsigned src, unsigned dst, int w) {
+    return mix64(((unsigned long long)src << 32 | dst) ^ mix64(0x9E3779B97F4A7C15ull + (unsigned)w));
+}
+
+// Multiset hash of the forward edges (sum of per-edge hashes), one warp per row.
+__global__ void k_hash_fwd(int n, const int *row_ptr, const int *col, const int *w, unsigned long long *out) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    unsigned long long h = 0;
+    for (int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n; v += nw) {
+        const int b = row_ptr[v], e = row_ptr[v + 1];
+        for (int k = b + lane; k < e; k += 32) h += edge_hash((unsigned)v, (unsigned)col[k], w[k]);
+    }
+    for (int d = 16; d; d >>= 1) h += __shfl_down_sync(FULL, h, d);
+    if (lane == 0) atomicAdd(out, h);
+}
+
+__global__ void k_hash_rev(int n, const int *rrow_ptr, const unsigned *rcol, const int *rw, unsigned long long *out) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    unsigned long long h = 0;
+    for (int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n; v += nw) {
+        const int b = rrow_ptr[v], e = rrow_ptr[v + 1];
+        for (int k = b + lane; k < e; k += 32) h += edge_hash(rcol[k] & 0x7fffffffu, (unsigned)v, rw[k]);
+    }
+    for (int d = 16; d; d >>= 1) h += __shfl_down_sync(FULL, h, d);
+    if (lane == 0) atomicAdd(out, h);
+}
+
+static size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+static bool is_device_ptr(const void *p) {
+    cudaPointerAttributes attr{};
+    bool dev = p && cudaPointerGetAttributes(&attr, p) == cudaSuccess &&
+               (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    return dev;
+}
+
+static eg_status destroy(eg_arena *a) {
+    if (!a) return EG_OK;
+    free_state(a->st32);
+    free_state(a->st64);
+    if (a->block) cudaFree(a->block);
+    if (a->ev0) cudaEventDestroy(a->ev0);
+    if (a->ev1) cudaEventDestroy(a->ev1);
+    if (a->evk) cudaEventDestroy(a->evk);
+    if (a->host_ctrl) cudaFreeHost(a->host_ctrl);
+    delete a;
+    return EG_OK;
+}
+
+static eg_status create(int64_t n64, int64_t m64, const int64_t *row_ptr, const int32_t *col, const int32_t *w,
+                        const int64_t *rrow_ptr, const int32_t *rcol, const int32_t *rw,
+                        const uint32_t *owner_bits, uint32_t flags, eg_arena **out) {
+    if (!out) {
+        set_error("out is NULL");
+        return EG_ERR_INVALID;
+    }
+    *out = nullptr;
+    if (n64 < 1 || n64 >= (1LL << 31) - 1 || m64 < n64 || m64 >= (1LL << 31) - 1) {
+        set_error("need 1 <= n < 2^31 - 1 and n <= m < 2^31 - 1 (got n=%lld m=%lld)", (long long)n64,
+                  (long long)m64);
+        return m64 < n64 && n64 >= 1 && m64 >= 0 ? EG_ERR_NOT_TOTAL : EG_ERR_INVALID;
+    }
+    if (!row_ptr || !col || !w || !owner_bits) {
+        set_error("row_ptr, col, w and owner_bits are required");
+        return EG_ERR_INVALID;
+    }
+    const bool have_rev = rrow_ptr || rcol || rw;
+    if (have_rev && !(rrow_ptr && rcol && rw)) {
+        set_error("rrow_ptr, rcol and rw must be given together or all NULL");
+        return EG_ERR_INVALID;
+    }
+    if ((flags & ~EG_INPUT_DEVICE) != 0) {
+        set_error("unknown flags 0x%x", flags);
+        return EG_ERR_INVALID;
+    }
+    const bool dev_in = (flags & EG_INPUT_DEVICE) != 0;
+    if (dev_in && !is_device_ptr(row_ptr)) {
+        set_error("EG_INPUT_DEVICE given but row_ptr is not device memory");
+        return EG_ERR_INVALID;
+    }
+    const cudaMemcpyKind kind = dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const int n = (int)n64, m = (int)m64;
+    const size_t words = ((size_t)n + 31) / 32;
+
+    eg_arena *a = new (std::nothrow) eg_arena();
+    if (!a) {
+        set_error("host allocation failed");
+        return EG_ERR_OOM;
+    }
+    cudaGetDevice(&a->device);
+    a->n = n;
+    a->m = m;
+    eg_status rc = EG_OK;
+    char *tmp = nullptr;
+#define TRY(expr)                     \
+    do {                              \
+        cudaError_t _e = (expr);      \
+        if (_e != cudaSuccess) {      \
+            set_error("%s failed: %s", #expr, cudaGetErrorString(_e)); \
+            rc = _e == cudaErrorMemoryAllocation ? EG_ERR_OOM : EG_ERR_CUDA; \
+            goto fail;                \
+        }                             \
+    } while (0)
+    {
+        // persistent arrays
+        size_t off = 0;
+        const size_t o_rp = off; off = align_up(off + ((size_t)n + 1) * 4);
+        const size_t o_col = off; off = align_up(off + (size_t)m * 4);
+        const size_t o_w = off; off = align_up(off + (size_t)m * 4);
+        const size_t o_rrp = off; off = align_up(off + ((size_t)n + 1) * 4);
+        const size_t o_rcol = off; off = align_up(off + (size_t)m * 4);
+        const size_t o_rw = off; off = align_up(off + (size_t)m * 4);
+        const size_t o_own = off; off = align_up(off + words * 4);
+        char *blk = nullptr;
+        unsigned *hflags = nullptr;
+        unsigned long long hh[2] = {0, 0};
+        const cudaStream_t s = 0;
+        TRY(cudaMalloc((void **)&blk, off));
+        a->block = blk;
+        int *rp32 = (int *)(blk + o_rp);
+        int *dcol = (int *)(blk + o_col);
+        int *dw = (int *)(blk + o_w);
+        int *rrp32 = (int *)(blk + o_rrp);
+        unsigned *drcol = (unsigned *)(blk + o_rcol);
+        int *drw = (int *)(blk + o_rw);
+        unsigned *down = (unsigned *)(blk + o_own);
+        // temporaries: int64 offsets (x2), flags, hashes, scan scratch, fill pointers
+        size_t t = 0;
+        const size_t t_rp = t; t = align_up(t + ((size_t)n + 1) * 8);
+        const size_t t_rrp = t; t = align_up(t + ((size_t)n + 1) * 8);
+        const size_t t_flags = t; t = align_up(t + 64);
+        const size_t t_scan = t; t = align_up(t + ((size_t)n / 1024 + 64) * 4 * 2);
+        const size_t t_fill = t; t = align_up(t + ((size_t)n + 1) * 4);
+        TRY(cudaMalloc((void **)&tmp, t));
+        long long *rp64 = (long long *)(tmp + t_rp);
+        long long *rrp64 = (long long *)(tmp + t_rrp);
+        unsigned *dflags = (unsigned *)(tmp + t_flags);
+        unsigned long long *dhash = (unsigned long long *)(tmp + t_flags + 16);
+        int *scan_scratch = (int *)(tmp + t_scan);
+        int *fill = (int *)(tmp + t_fill);
+
+        TRY(cudaMemsetAsync(dflags, 0, 64, s));
+        TRY(cudaMemcpyAsync(rp64, row_ptr, ((size_t)n + 1) * 8, kind, s));
+        TRY(cudaMemcpyAsync(dcol, col, (size_t)m * 4, kind, s));
+        TRY(cudaMemcpyAsync(dw, w, (size_t)m * 4, kind, s));
+        TRY(cudaMemcpyAsync(down, owner_bits, words * 4, kind, s));
+        {
+            const int g = (int)std::min<long long>(((long long)n + 256) / 256, 8192);
+            const int ge = (int)std::min<long long>(((long long)m + 255) / 256, 8192);
+            k_check_rows<<<g, 256, 0, s>>>(rp64, n, m, rp32, dflags);
+            k_check_cols<<<ge, 256, 0, s>>>(dcol, m, n, dflags, BAD_COL);
+            TRY(cudaGetLastError());
+            if (have_rev) {
+                TRY(cudaMemcpyAsync(rrp64, rrow_ptr, ((size_t)n + 1) * 8, kind, s));
+                TRY(cudaMemcpyAsync(drcol, rcol, (size_t)m * 4, kind, s));
+                TRY(cudaMemcpyAsync(drw, rw, (size_t)m * 4, kind, s));
+                k_check_rows<<<g, 256, 0, s>>>(rrp64, n, m, rrp32, dflags + 1);
+                k_check_cols<<<ge, 256, 0, s>>>((const int *)drcol, m, n, dflags, BAD_RCOL);
+                TRY(cudaGetLastError());
+            }
+            TRY(cudaMallocHost((void **)&hflags, 16));
+            TRY(cudaMemcpyAsync(hflags, dflags, 8, cudaMemcpyDeviceToHost, s));
+            TRY(cudaStreamSynchronize(s));
+            const unsigned fl = hflags[0], rfl = hflags[1] & BAD_ROWPTR;
+            cudaFreeHost(hflags);
+            hflags = nullptr;
+            if (fl & (BAD_ROWPTR | BAD_COL)) {
+                set_error("malformed forward CSR (%s)", (fl & BAD_ROWPTR) ? "row_ptr" : "col out of range");
+                rc = EG_ERR_INVALID;
+                goto fail;
+            }
+            if (fl & NOT_TOTAL) {
+                set_error("arena is not total: some vertex has no successor");
+                rc = EG_ERR_NOT_TOTAL;
+                goto fail;
+            }
+            if (rfl || (fl & BAD_RCOL)) {
+                set_error("malformed reverse CSR");
+                rc = EG_ERR_INVALID;
+                goto fail;
+            }
+            if (!have_rev) {
+                TRY(cudaMemsetAsync(rrp32, 0, ((size_t)n + 1) * 4, s));
+                k_count_in<<<ge, 256, 0, s>>>(dcol, m, rrp32);
+                TRY(cudaGetLastError());
+                TRY(exclusive_scan(rrp32, n + 1, scan_scratch, s));
+                TRY(cudaMemcpyAsync(fill, rrp32, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+                const int gw = (int)std::min<long long>(((long long)n + 7) / 8, 1 << 16);
+                k_scatter<<<gw, 256, 0, s>>>(n, rp32, dcol, dw, down, fill, drcol, drw);
+                TRY(cudaGetLastError());
+            } else {
+                const int gw = (int)std::min<long long>(((long long)n + 7) / 8, 1 << 16);
+                k_hash_fwd<<<gw, 256, 0, s>>>(n, rp32, dcol, dw, dhash);
+                k_hash_rev<<<gw, 256, 0, s>>>(n, rrp32, drcol, drw, dhash + 1);
+                k_tag_rcol<<<ge, 256, 0, s>>>(m, down, drcol);
+                TRY(cudaGetLastError());
+                TRY(cudaMemcpyAsync(hh, dhash, 16, cudaMemcpyDeviceToHost, s));
+            }
+            TRY(cudaStreamSynchronize(s));
+            cudaFree(tmp);
+            tmp = nullptr;
+            if (have_rev && hh[0] != hh[1]) {
+                set_error("reverse CSR does not hold the same edges as the forward CSR");
+                rc = EG_ERR_INVALID;
+                goto fail;
+            }
+        }
+        a->d.n = n;
+        a->d.m = m;
+        a->d.row_ptr = rp32;
+        a->d.col = dcol;
+        a->d.w = dw;
+        a->d.rrow_ptr = rrp32;
+        a->d.rcol = drcol;
+        a->d.rw = drw;
+        a->d.owner_bits = down;
+        TRY(cudaEventCreate(&a->ev0));
+        TRY(cudaEventCreate(&a->ev1));
+        TRY(cudaEventCreate(&a->evk));
+        TRY(cudaMallocHost(&a->host_ctrl, sizeof(Ctrl)));
+        long long C = 0, wm = 0;
+        rc = compute_bound(a, 1, 0, &C, &wm, s);
+        if (rc != EG_OK) goto fail;
+    }
+#undef TRY
+    *out = a;
+    return EG_OK;
+fail:
+    if (tmp) cudaFree(tmp);
+    destroy(a);
+    return rc;
+}
+
+}  // namespace eg
+
+extern "C" {
+
+eg_status eg_create(int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col, const int32_t *w,
+                    const int64_t *rrow_ptr, const int32_t *rcol, const int32_t *rw, const uint32_t *owner_bits,
+                    uint32_t flags, eg_arena **out) {
+    eg::clear_error();
+    try {
+        return eg::create(n, m, row_ptr, col, w, rrow_ptr, rcol, rw, owner_bits, flags, out);
+    } catch (...) {
+        eg::set_error("unexpected exception in eg_create");
+        return EG_ERR_INVALID;
+    }
+}
+
+eg_status eg_destroy(eg_arena *arena) {
+    eg::clear_error();
+    return eg::destroy(arena);
+}
+
+eg_status eg_bound(eg_arena *arena, int64_t w_scale, int64_t w_shift, int64_t *C, int64_t *max_abs_w) {
+    eg::clear_error();
+    if (!arena) {
+        eg::set_error("arena is NULL");
+        return EG_ERR_INVALID;
+    }
+    long long c = 0, wm = 0;
+    eg_status rc = eg::compute_bound(arena, w_scale, w_shift, &c, &wm, 0);
+    if (rc != EG_OK) return rc;
+    if (C) *C = c;
+    if (max_abs_w) *max_abs_w = wm;
+    return EG_OK;
+}
+
+eg_status eg_solve_credit(eg_arena *arena, int32_t credit_bits, int64_t w_scale, int64_t w_shift,
+                          void *credits_out, eg_stats *st, void *cuda_stream, int64_t max_rounds) {
+    eg::clear_error();
+    if (!arena || !credits_out) {
+        eg::set_error("arena and credits_out are required");
+        return EG_ERR_INVALID;
+    }
+    try {
+        return eg::solve(arena, credit_bits, w_scale, w_shift, credits_out, st, (cudaStream_t)cuda_stream,
+                         max_rounds);
+    } catch (...) {
+        eg::set_error("unexpected exception in eg_solve_credit");
+        return EG_ERR_INVALID;
+    }
+}
+
+const char *eg_last_error(void) { return eg::g_err; }
+
+const char *eg_version(void) { return "eg-gb300 0.1"; }
+
+}  // extern "C"

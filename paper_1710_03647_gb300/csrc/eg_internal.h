@@ -1,0 +1,102 @@
+// Internal definitions shared by the solver's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/eg.h"
+
+namespace eg {
+
+// Thread-local message behind eg_last_error().
+void set_error(const char *fmt, ...);
+void clear_error();
+
+#define EG_CUDA_TRY(expr)                                                                    \
+    do {                                                                                     \
+        cudaError_t _e = (expr);                                                             \
+        if (_e != cudaSuccess) {                                                             \
+            ::eg::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(_e), __FILE__, \
+                            __LINE__);                                                       \
+            return _e == cudaErrorMemoryAllocation ? EG_ERR_OOM : EG_ERR_CUDA;               \
+        }                                                                                    \
+    } while (0)
+
+// Control block of one solve, in device memory.  Lists for round r live in
+// buffer r & 1; their packed counters in slot r % 3 (low 32 bits: entries,
+// high 32 bits: total work = edges to scan).
+struct Ctrl {
+    unsigned long long pull_ctr[3];
+    unsigned long long push_ctr[3];
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    int status;
+    int pad;
+    unsigned long long rounds, lifts, pushes, relax, enqueues;
+};
+
+// Read-only arena data on the device (int32 offsets: m < 2^31).
+struct DevArena {
+    int n;
+    int m;
+    const int *row_ptr;         // n + 1
+    const int *col;             // m
+    const int *w;               // m
+    const int *rrow_ptr;        // n + 1
+    const unsigned *rcol;       // m: predecessor id | (owner(pred) is V1) << 31
+    const int *rw;              // m: w(pred, v)
+    const unsigned *owner_bits; // ceil(n / 32)
+};
+
+// Weight view w' = scale * w - shift and the bound C of that view.
+struct WeightView {
+    long long scale;
+    long long shift;
+    long long C;
+};
+
+// Mutable per-solve state for one credit width.
+struct DevState {
+    void *f;           // int32 or int64 credits, n
+    int *pull_items[2];
+    int *pull_offs[2];
+    int *push_items[2];
+    int *push_offs[2];
+    unsigned *bits[2]; // dedupe bitmaps, ceil(n/32) words
+    void *acc;         // partial minima of split player-0 lifts, n (TOP when idle)
+    int *acc_done;     // edges accounted into acc, n (0 when idle)
+    Ctrl *ctrl;
+};
+
+struct StateBuffers {
+    int bits = 0;      // 0 = not allocated, else 32 / 64
+    bool dirty = true; // scratch (acc, acc_done, bitmaps) needs resetting
+    DevState d{};
+    void *block = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace eg
+
+struct eg_arena {
+    int device = 0;
+    int n = 0;
+    int m = 0;
+    void *block = nullptr;  // one allocation holding the read-only arrays
+    eg::DevArena d{};
+    long long C_plain = -1, wmax_plain = -1;  // bound and max |w| for scale 1, shift 0
+    eg::StateBuffers st32, st64;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, evk = nullptr;
+    void *host_ctrl = nullptr;  // pinned copy of Ctrl
+};
+
+namespace eg {
+// Implemented in eg_solve.cu
+eg_status compute_bound(eg_arena *a, long long scale, long long shift, long long *C, long long *wmax,
+                        cudaStream_t s);
+eg_status solve(eg_arena *a, int credit_bits, long long scale, long long shift, void *out, eg_stats *st,
+                cudaStream_t s, long long max_rounds);
+eg_status free_state(StateBuffers &sb);
+}  // namespace eg

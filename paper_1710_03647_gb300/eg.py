@@ -1,0 +1,186 @@
+"""Thin ctypes binding of libeg.so (include/eg.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA library.
+Functions keep the C names (eg_create, eg_solve_credit, ...) and take numpy
+arrays (host) or integer device addresses (e.g. torch.Tensor.data_ptr()).
+The library is loaded from this package's _lib/ directory; if it is missing
+the import of this module fails loudly -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libeg.so")
+
+EG_OK = 0
+EG_PENDING = 1
+EG_ERR_INVALID = -1
+EG_ERR_NOT_TOTAL = -2
+EG_ERR_OVERFLOW = -3
+EG_ERR_OOM = -4
+EG_ERR_CUDA = -5
+EG_ERR_TIMEOUT = -6
+EG_ERR_BUDGET = -7
+EG_ERR_BUSY = -8
+EG_TOP32 = np.iinfo(np.int32).max
+EG_TOP64 = np.iinfo(np.int64).max
+EG_INPUT_DEVICE = 1
+
+STATUS_NAMES = {0: "EG_OK", 1: "EG_PENDING", -1: "EG_ERR_INVALID", -2: "EG_ERR_NOT_TOTAL",
+                -3: "EG_ERR_OVERFLOW", -4: "EG_ERR_OOM", -5: "EG_ERR_CUDA", -6: "EG_ERR_TIMEOUT",
+                -7: "EG_ERR_BUDGET", -8: "EG_ERR_BUSY"}
+
+
+class eg_stats(ctypes.Structure):
+    _fields_ = [("C", ctypes.c_int64), ("credit_bits", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("rounds", ctypes.c_int64), ("lifts", ctypes.c_int64), ("pushes", ctypes.c_int64),
+                ("relaxations", ctypes.c_int64), ("enqueues", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("fixpoint_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class EGError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+# exported symbol -> (restype, argtypes); the header's declarations
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+SIGNATURES = {
+    "eg_create": (_I32, [_I64, _I64, _P, _P, _P, _P, _P, _P, _P, ctypes.c_uint32, ctypes.POINTER(_P)]),
+    "eg_destroy": (_I32, [_P]),
+    "eg_bound": (_I32, [_P, _I64, _I64, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "eg_solve_credit": (_I32, [_P, _I32, _I64, _I64, _P, ctypes.POINTER(eg_stats), _P, _I64]),
+    "eg_last_error": (ctypes.c_char_p, []),
+    "eg_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads libeg.so and declares every entry point; raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"libeg.so not built at {path}; run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def eg_last_error() -> str:
+    return load().eg_last_error().decode()
+
+
+def eg_version() -> str:
+    return load().eg_version().decode()
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise EGError(rc, eg_last_error())
+    return rc
+
+
+def _addr(x, dtype):
+    """Host numpy array (kept alive by the caller) or an int device address."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    a = np.ascontiguousarray(x, dtype=dtype)
+    if a is not x:
+        raise TypeError(f"expected a contiguous {np.dtype(dtype)} array")
+    return a.ctypes.data
+
+
+def eg_create(n, m, row_ptr, col, w, rrow_ptr=None, rcol=None, rw=None, owner_bits=None, flags=0):
+    """Returns an opaque arena handle (int).  Host arrays must already have
+    the exact dtypes: int64 row_ptr, int32 col / w, uint32 owner_bits."""
+    out = _P()
+    rc = load().eg_create(n, m, _addr(row_ptr, np.int64), _addr(col, np.int32), _addr(w, np.int32),
+                          _addr(rrow_ptr, np.int64), _addr(rcol, np.int32), _addr(rw, np.int32),
+                          _addr(owner_bits, np.uint32), flags, ctypes.byref(out))
+    _check(rc)
+    return out.value
+
+
+def eg_destroy(arena) -> None:
+    _check(load().eg_destroy(arena))
+
+
+def eg_bound(arena, w_scale: int = 1, w_shift: int = 0) -> tuple[int, int]:
+    C, wm = _I64(), _I64()
+    _check(load().eg_bound(arena, w_scale, w_shift, ctypes.byref(C), ctypes.byref(wm)))
+    return C.value, wm.value
+
+
+def eg_solve_credit(arena, credit_bits, w_scale, w_shift, credits_out, stream=None, max_rounds=0,
+                    raise_on_error=True):
+    """credits_out: numpy array (host) or device address / tensor of the
+    right width.  Returns (status, eg_stats)."""
+    st = eg_stats()
+    if isinstance(credits_out, np.ndarray):
+        want = np.int32 if credit_bits == 32 else np.int64
+        if credits_out.dtype != want or not credits_out.flags.c_contiguous:
+            raise TypeError(f"credits_out must be a contiguous {np.dtype(want)} array")
+        out_ptr = credits_out.ctypes.data
+    else:
+        out_ptr = _addr(credits_out, None)
+    rc = load().eg_solve_credit(arena, credit_bits, w_scale, w_shift, out_ptr, ctypes.byref(st),
+                                stream if stream is not None else None, max_rounds)
+    if raise_on_error:
+        _check(rc)
+    return rc, st
+
+
+class Arena:
+    """Owns an eg_arena built from a gen.Arena-like object (host numpy arrays)."""
+
+    def __init__(self, a, with_reverse=None):
+        self.n, self.m = int(a.n), int(a.m)
+        rev = with_reverse or (None, None, None)
+        self.handle = eg_create(self.n, self.m, np.ascontiguousarray(a.row_ptr, np.int64),
+                                np.ascontiguousarray(a.col, np.int32), np.ascontiguousarray(a.w, np.int32),
+                                *rev, owner_bits=np.ascontiguousarray(a.owner_bits, np.uint32))
+
+    def solve(self, credit_bits=0, w_scale=1, w_shift=0, stream=None, max_rounds=0):
+        out = np.empty(self.n, dtype=np.int32 if credit_bits == 32 else np.int64)
+        _, st = eg_solve_credit(self.handle, credit_bits, w_scale, w_shift, out, stream, max_rounds)
+        return out, st
+
+    def bound(self, w_scale=1, w_shift=0):
+        return eg_bound(self.handle, w_scale, w_shift)
+
+    def close(self):
+        if self.handle:
+            eg_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
