@@ -61,6 +61,7 @@ typedef struct eg_server eg_server;
  * their predecessors; rounds counts frontier rounds (Algorithm 3's loop). */
 typedef struct eg_stats {
     int64_t C;             /* the bound M_G of the (mapped) weights */
+    int64_t seeded;        /* vertices the warm start set to TOP (0 without it) */
     int32_t credit_bits;   /* width the solve computed in: 32 or 64 */
     int32_t status;        /* the solve's eg_status */
     int64_t rounds;
@@ -128,6 +129,34 @@ eg_status eg_bound(eg_arena *arena, int64_t w_scale, int64_t w_shift, int64_t *C
  */
 eg_status eg_solve_credit(eg_arena *arena, int32_t credit_bits, int64_t w_scale, int64_t w_shift,
                           void *credits_out, eg_stats *st, void *cuda_stream, int64_t max_rounds);
+
+/*
+ * eg_set_option -- per-arena settings of later solves.  None of them changes
+ * a result: they change only how fast the least fixpoint is reached.
+ *
+ *   EG_OPT_LOCAL_WINDOWS (default 256): per-warp budget, per round, of
+ *     32-entry windows worked through the warp's local worklist, which
+ *     carries a rise on to the predecessors within the same round; 0 turns
+ *     this off (one hop per round, as in Algorithm 3).
+ *   EG_OPT_LOCAL_MAXDEG (default 64): largest degree of a vertex handled
+ *     through the local worklist.
+ *   EG_OPT_WARM_START (default 1): before lifting, set f = TOP on player-1
+ *     vertices that lie on a negative cycle of player-1 vertices of length
+ *     1 or 2 (under the weight map).  Player 1 keeps the play on such a
+ *     cycle forever, so these vertices are in W1 (Lemma "EGcycles" and
+ *     memoryless determinacy, Sec. 3) and TOP is their least-fixpoint
+ *     value: the start stays below the least fixpoint and the result is
+ *     unchanged.  0 starts from f = 0 everywhere, as the paper does.
+ *   EG_OPT_SEED_MAX_PAIRS (default 4096): the warm start skips a vertex
+ *     whose out-degree times in-degree exceeds this.
+ *
+ * EG_ERR_INVALID for an unknown option or a negative value.
+ */
+#define EG_OPT_LOCAL_WINDOWS 1
+#define EG_OPT_LOCAL_MAXDEG 2
+#define EG_OPT_WARM_START 3
+#define EG_OPT_SEED_MAX_PAIRS 4
+eg_status eg_set_option(eg_arena *arena, int32_t option, int64_t value);
 
 /* eg_last_error -- message of the calling thread's last failure ("" if none). */
 const char *eg_last_error(void);

@@ -431,6 +431,32 @@ eg_status eg_solve_credit(eg_arena *arena, int32_t credit_bits, int64_t w_scale,
     }
 }
 
+eg_status eg_set_option(eg_arena *arena, int32_t option, int64_t value) {
+    eg::clear_error();
+    if (!arena) {
+        eg::set_error("arena is NULL");
+        return EG_ERR_INVALID;
+    }
+    if (value < 0 || value > (1LL << 30)) {
+        eg::set_error("option value %lld out of range", (long long)value);
+        return EG_ERR_INVALID;
+    }
+    switch (option) {
+    case EG_OPT_LOCAL_WINDOWS: arena->local_windows = (int)value; break;
+    case EG_OPT_LOCAL_MAXDEG: arena->local_maxdeg = (int)value; break;
+    case EG_OPT_WARM_START:
+        if (value > 1) {
+            eg::set_error("EG_OPT_WARM_START takes 0 or 1");
+            return EG_ERR_INVALID;
+        }
+        arena->warm_start = (int)value;
+        break;
+    case EG_OPT_SEED_MAX_PAIRS: arena->seed_max_pairs = value; break;
+    default: eg::set_error("unknown option %d", option); return EG_ERR_INVALID;
+    }
+    return EG_OK;
+}
+
 const char *eg_last_error(void) { return eg::g_err; }
 
 const char *eg_version(void) { return "eg-gb300 0.1"; }

@@ -56,6 +56,22 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     return v;
 }
 
+// Bitmap updates that order the credit accesses around them: a vertex is
+// marked queued with a release (after the rise that queued it) and unmarked
+// with an acquire (before its credits are read), so a rise absorbed by an
+// already-queued vertex is seen when that vertex is processed.
+__device__ __forceinline__ unsigned atom_or_release(unsigned *p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.release.gpu.global.or.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ unsigned atom_and_acquire(unsigned *p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acquire.gpu.global.and.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

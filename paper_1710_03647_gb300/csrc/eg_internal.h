@@ -34,7 +34,7 @@ struct Ctrl {
     unsigned int bar_gen;
     int status;
     int pad;
-    unsigned long long rounds, lifts, pushes, relax, enqueues;
+    unsigned long long rounds, lifts, pushes, relax, enqueues, seeded;
 };
 
 // Read-only arena data on the device (int32 offsets: m < 2^31).
@@ -64,7 +64,9 @@ struct DevState {
     int *pull_offs[2];
     int *push_items[2];
     int *push_offs[2];
-    unsigned *bits[2]; // dedupe bitmaps, ceil(n/32) words
+    unsigned *bits_pull[2]; // dedupe bitmaps of the pull lists, ceil(n/32) words
+    unsigned *bits_push[2]; // dedupe bitmaps of the push lists
+    unsigned *seed_bits;    // warm-start marks, ceil(n/32) words
     void *acc;         // partial minima of split player-0 lifts, n (TOP when idle)
     int *acc_done;     // edges accounted into acc, n (0 when idle)
     Ctrl *ctrl;
@@ -90,6 +92,10 @@ struct eg_arena {
     eg::StateBuffers st32, st64;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evk = nullptr;
     void *host_ctrl = nullptr;  // pinned copy of Ctrl
+    int local_windows = 256;    // per-warp local worklist budget per round (0 disables chaining)
+    int local_maxdeg = 64;      // largest degree of a vertex handled through the local worklist
+    int warm_start = 1;         // TOP on player-1 negative cycles of length <= 2 before lifting
+    long long seed_max_pairs = 4096;
 };
 
 namespace eg {

@@ -43,6 +43,7 @@
 namespace eg {
 
 constexpr unsigned long long BARRIER_LIMIT_NS = 5000000000ull;  // 5 s per wait
+constexpr int LOCAL_CAP = 256;  // entries of a warp's local worklist
 
 __device__ __forceinline__ int xchg(int *p, int v) { return atomicExch(p, v); }
 __device__ __forceinline__ long long xchg(long long *p, long long v) {
@@ -58,11 +59,15 @@ struct Args {
     int *pull_offs[2];
     int *push_items[2];
     int *push_offs[2];
-    unsigned *bits[2];
+    unsigned *bits_pull[2];  // dedupe of the pull list of round parity k
+    unsigned *bits_push[2];  // dedupe of the push list of round parity k
+    const unsigned *seed_bits;  // warm start: vertices that start at TOP (or null)
     T *acc;
     int *acc_done;
     Ctrl *ctrl;
     long long max_rounds;
+    int local_windows;  // per-warp budget of local windows per round (0: no chaining)
+    int local_maxdeg;   // largest degree a vertex may have to be chained locally
 };
 
 // ---------------------------------------------------------------------------
@@ -96,6 +101,62 @@ __global__ void k_fill(T *p, long long n, T v) {
 }
 
 // ---------------------------------------------------------------------------
+// Warm start.  A player-1 vertex u on a cycle of player-1 vertices whose
+// weight (under the weight view) is negative is won by player 1: player 1
+// can keep the play on that cycle forever, so every credit runs out
+// (Lemma "EGcycles" with memoryless determinacy, Sec. 3).  Its least-EPM
+// value is TOP, so starting it at TOP stays below the least fixpoint.
+// Looked for: negative self-loops and 2-cycles u -> t -> u.  One warp per
+// player-1 vertex compares each out-edge (u, t) with each in-edge (s, u)
+// for s == t; vertices with out-degree x in-degree above max_pairs are
+// skipped (the warm start is optional, missing a cycle only costs time).
+__global__ void k_seed(DevArena A, WeightView W, long long max_pairs, unsigned *seed_bits,
+                       unsigned long long *count) {
+    const int lane = lane_id();
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    unsigned found_total = 0;
+    for (int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < A.n; u += nw) {
+        if (!((__ldg(A.owner_bits + (u >> 5)) >> (u & 31)) & 1u)) continue;
+        const int ob = __ldg(A.row_ptr + u), oe = __ldg(A.row_ptr + u + 1);
+        const int ib = __ldg(A.rrow_ptr + u), ie = __ldg(A.rrow_ptr + u + 1);
+        if ((long long)(oe - ob) * (long long)(ie - ib) > max_pairs) continue;
+        bool found = false;
+        for (int kb = ob; kb < oe; kb += 32) {
+            const int k = kb + lane;
+            int t = -1;
+            long long wt = 0;
+            if (k < oe) {
+                t = __ldg(A.col + k);
+                wt = wmap(__ldg(A.w + k), W);
+                if (t == u && wt < 0) found = true;  // negative self-loop
+            }
+            for (int jb = ib; jb < ie; jb += 32) {
+                const int j = jb + lane;
+                unsigned sv = 0;
+                long long ws = 0;
+                if (j < ie) {
+                    sv = __ldg(A.rcol + j);
+                    ws = wmap(__ldg(A.rw + j), W);
+                }
+                const int cnt = min(32, ie - jb);
+                for (int q = 0; q < cnt; ++q) {
+                    const unsigned sq = __shfl_sync(FULL, sv, q);
+                    const long long wq = __shfl_sync(FULL, ws, q);
+                    if ((sq & P1_FLAG) && (int)(sq & 0x7fffffffu) == t && (int)(sq & 0x7fffffffu) != u &&
+                        wt + wq < 0)
+                        found = true;
+                }
+            }
+        }
+        if (__any_sync(FULL, found)) {
+            if (lane == 0) atomicOr(seed_bits + (u >> 5), 1u << (u & 31));
+            ++found_total;
+        }
+    }
+    if (lane == 0 && found_total) atomicAdd(count, (unsigned long long)found_total);
+}
+
+// ---------------------------------------------------------------------------
 // Initialisation (Algorithm 3, lines 1-3, with the first lift folded in):
 // f(v) = delta(0, v)(v), i.e. max(0, -w') maximised (V1) or minimised (V0)
 // over v's edges.  That is positive exactly for the initial set L of
@@ -114,9 +175,13 @@ __global__ void __launch_bounds__(THREADS) k_init(Args<T> a) {
             const bool p1 = (__ldg(A.owner_bits + (v >> 5)) >> (v & 31)) & 1u;
             const int b = __ldg(A.row_ptr + v), e = __ldg(A.row_ptr + v + 1);
             T g = p1 ? T(0) : Cred<T>::TOP;
-            for (int k = b; k < e; ++k) {
-                T t = ominus<T>(T(0), wmap(__ldg(A.w + k), a.W), a.W.C);
-                g = p1 ? max(g, t) : min(g, t);
+            if (a.seed_bits && ((a.seed_bits[v >> 5] >> (v & 31)) & 1u)) {
+                g = Cred<T>::TOP;
+            } else {
+                for (int k = b; k < e; ++k) {
+                    T t = ominus<T>(T(0), wmap(__ldg(A.w + k), a.W), a.W.C);
+                    g = p1 ? max(g, t) : min(g, t);
+                }
             }
             a.f[v] = g;
             work = __ldg(A.rrow_ptr + v + 1) - __ldg(A.rrow_ptr + v);
@@ -124,6 +189,234 @@ __global__ void __launch_bounds__(THREADS) k_init(Args<T> a) {
             item = (unsigned)v | (p1 ? P1_FLAG : 0u);
         }
         warp_append(want, item, work, &a.ctrl->push_ctr[0], a.push_items[0], a.push_offs[0]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Window helpers.  A warp works on up to 32 list entries at a time, one per
+// lane; lane j holds its entry's first edge `beg` and the entry's offset `o`
+// in the warp's edge coordinates (non-decreasing over lanes; lanes without an
+// entry hold the window total).  Edge x belongs to the largest j with o_j <= x.
+
+__device__ __forceinline__ int owner_lane(int o, int xl) {
+    int j = 0;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const int oj = __shfl_sync(FULL, o, j + s);
+        if (oj <= xl) j += s;
+    }
+    return j;
+}
+
+// Exclusive warp scan of per-lane works; returns the total.
+__device__ __forceinline__ int warp_exclusive(int work, int &excl) {
+    const int lane = lane_id();
+    int incl = work;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int o = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += o;
+    }
+    excl = incl - work;
+    return __shfl_sync(FULL, incl, 31);
+}
+
+// Minimum of f(u) (-) w(v,u) over the edges [x0, stop) of the window, per
+// owning lane (TOP for lanes that own none of them).
+template <typename T>
+__device__ __forceinline__ T pull_min(const Args<T> &a, int beg, int o, int x0, int stop, T *red) {
+    const int lane = lane_id();
+    red[lane] = Cred<T>::TOP;
+    __syncwarp();
+    for (int xb = x0; xb < stop; xb += 32) {
+        const int xl = xb + lane;
+        const bool act = xl < stop;
+        const int j = owner_lane(o, xl);
+        const int bj = __shfl_sync(FULL, beg, j);
+        const int oj = __shfl_sync(FULL, o, j);
+        T t = Cred<T>::TOP;
+        if (act) {
+            const int e = bj + (xl - oj);
+            const int u = __ldg(a.A.col + e);
+            t = ominus<T>(ld_cg(a.f + u), wmap(__ldg(a.A.w + e), a.W), a.W.C);
+        }
+        const int key = act ? j : 32 + lane;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const T ov = __shfl_up_sync(FULL, t, d);
+            const int ok = __shfl_up_sync(FULL, key, d);
+            if (lane >= d && ok == key) t = min(t, ov);
+        }
+        const int nk = __shfl_down_sync(FULL, key, 1);
+        if (act && (lane == 31 || nk != key)) red[j] = min(red[j], t);
+        __syncwarp();
+    }
+    const T g = red[lane];
+    __syncwarp();
+    return g;
+}
+
+// Per-warp state of one round's push phase: the local worklist (a stack in
+// shared memory) and counters of the work done through it.
+template <typename T>
+struct Local {
+    int *stack;
+    int top;
+    bool on;
+    unsigned long long relax, lifts, pushes;
+};
+
+constexpr unsigned NEED_NONE = 0, NEED_PULL = 1, NEED_PUSH = 2;
+
+// Routes vertices that need work in this or the next round.  NEED_PULL: a
+// player-0 vertex that may lift; NEED_PUSH: a vertex whose rise must reach
+// its predecessors.  The next round's bitmap of that kind marks a vertex as
+// queued -- in some warp's local worklist or in the next round's list -- so a
+// vertex already queued absorbs the request (it reads fresh credits when it
+// is processed).  Newly queued small vertices go to the warp's local
+// worklist while it has room; the rest join the next round's lists.
+template <typename T>
+__device__ __forceinline__ void route(const Args<T> &a, int r, unsigned need, int p, int work, Local<T> &L) {
+    const int lane = lane_id();
+    bool fresh = false;
+    if (need != NEED_NONE) {
+        unsigned *bits = need == NEED_PULL ? a.bits_pull[(r + 1) & 1] : a.bits_push[(r + 1) & 1];
+        const unsigned bit = 1u << (p & 31);
+        fresh = !(atom_or_release(bits + (p >> 5), bit) & bit);
+    }
+    const bool local_ok = fresh && L.on && work <= a.local_maxdeg;
+    const unsigned lm = __ballot_sync(FULL, local_ok);
+    const int rank = __popc(lm & ((1u << lane) - 1u));
+    const int room = LOCAL_CAP - L.top;
+    bool placed = false;
+    if (local_ok && rank < room) {
+        L.stack[L.top + rank] = p | (need == NEED_PUSH ? (int)P1_FLAG : 0);
+        placed = true;
+    }
+    L.top += min(__popc(lm), room);
+    const bool gpull = fresh && !placed && need == NEED_PULL;
+    const bool gpush = fresh && !placed && need == NEED_PUSH;
+    const int nx = (r + 1) % 3;
+    warp_append(gpull, (unsigned)p, work, &a.ctrl->pull_ctr[nx], a.pull_items[(r + 1) & 1],
+                a.pull_offs[(r + 1) & 1]);
+    warp_append(gpush, (unsigned)p, work, &a.ctrl->push_ctr[nx], a.push_items[(r + 1) & 1],
+                a.push_offs[(r + 1) & 1]);
+}
+
+// Sends the values `val` of the window's entries over their in-edges
+// [x0, stop): t = val (-) w(p, v) for every predecessor p.  A player-1 p takes
+// max(f(p), t) (atomicMax) and, if it rose, needs a push; a player-0 p with
+// f(p) < t may need a lift.
+template <typename T>
+__device__ __forceinline__ void push_edges(const Args<T> &a, int r, int beg, int o, T val, int x0, int stop,
+                                           Local<T> &L) {
+    const int lane = lane_id();
+    for (int xb = x0; xb < stop; xb += 32) {
+        const int xl = xb + lane;
+        const bool act = xl < stop;
+        const int j = owner_lane(o, xl);
+        const int bj = __shfl_sync(FULL, beg, j);
+        const int oj = __shfl_sync(FULL, o, j);
+        const T vj = __shfl_sync(FULL, val, j);
+        unsigned need = NEED_NONE;
+        int p = 0, work = 0;
+        if (act) {
+            const int e = bj + (xl - oj);
+            const unsigned pr = __ldg(a.A.rcol + e);
+            p = (int)(pr & 0x7fffffffu);
+            const T t = ominus<T>(vj, wmap(__ldg(a.A.rw + e), a.W), a.W.C);
+            if (t > ld_cg(a.f + p)) {
+                if (pr & P1_FLAG) {
+                    if (t > atomicMax(a.f + p, t)) {
+                        work = __ldg(a.A.rrow_ptr + p + 1) - __ldg(a.A.rrow_ptr + p);
+                        if (work > 0) need = NEED_PUSH;
+                    }
+                } else {
+                    work = __ldg(a.A.row_ptr + p + 1) - __ldg(a.A.row_ptr + p);
+                    need = NEED_PULL;
+                }
+            }
+        }
+        route<T>(a, r, need, p, work, L);
+    }
+}
+
+// Empties the warp's local worklist: windows of up to 32 entries, each a
+// lift of its player-0 entries (in place, atomicMax) followed by a push of
+// every entry that rose and of the player-1 entries.  Runs for at most
+// a.local_windows windows, then hands what is left to the next round.
+template <typename T>
+__device__ void drain_local(const Args<T> &a, int r, T *red, Local<T> &L) {
+    const int lane = lane_id();
+    int windows = 0;
+    while (L.top > 0) {
+        if (windows >= a.local_windows) L.on = false;
+        ++windows;
+        const int take = min(32, L.top);
+        const bool have = lane < take;
+        const int raw = have ? L.stack[L.top - 1 - lane] : 0;
+        __syncwarp();
+        L.top -= take;
+        const int v = raw & 0x7fffffff;
+        const bool is_push = have && (raw & (int)P1_FLAG);
+        const bool is_pull = have && !(raw & (int)P1_FLAG);
+        if (!L.on) {  // budget spent: the entries (still marked) join the next round's lists
+            const int work = !have ? 0
+                             : is_pull ? __ldg(a.A.row_ptr + v + 1) - __ldg(a.A.row_ptr + v)
+                                       : __ldg(a.A.rrow_ptr + v + 1) - __ldg(a.A.rrow_ptr + v);
+            const int nx = (r + 1) % 3;
+            warp_append(is_pull, (unsigned)v, work, &a.ctrl->pull_ctr[nx], a.pull_items[(r + 1) & 1],
+                        a.pull_offs[(r + 1) & 1]);
+            warp_append(is_push, (unsigned)v, work, &a.ctrl->push_ctr[nx], a.push_items[(r + 1) & 1],
+                        a.push_offs[(r + 1) & 1]);
+            continue;
+        }
+        if (have) {  // unmark before reading credits
+            unsigned *bits = is_pull ? a.bits_pull[(r + 1) & 1] : a.bits_push[(r + 1) & 1];
+            atom_and_acquire(bits + (v >> 5), ~(1u << (v & 31)));
+        }
+        // lifts
+        int pbeg = 0, pwork = 0;
+        if (is_pull) {
+            pbeg = __ldg(a.A.row_ptr + v);
+            pwork = __ldg(a.A.row_ptr + v + 1) - pbeg;
+        }
+        int po;
+        const int ptotal = warp_exclusive(pwork, po);
+        T g = Cred<T>::TOP;
+        if (ptotal > 0) g = pull_min<T>(a, pbeg, po, 0, ptotal, red);
+        bool rose = is_push;
+        T val = T(0);
+        if (is_pull) {
+            rose = g > atomicMax(a.f + v, g);
+            val = g;
+        } else if (is_push) {
+            val = ld_cg(a.f + v);
+        }
+        L.relax += ptotal;
+        L.lifts += __popc(__ballot_sync(FULL, is_pull));
+        // pushes: small ones here, large ones to the next round
+        int qbeg = 0, qwork = 0;
+        if (rose) {
+            qbeg = __ldg(a.A.rrow_ptr + v);
+            qwork = __ldg(a.A.rrow_ptr + v + 1) - qbeg;
+        }
+        const bool big = rose && qwork > a.local_maxdeg;
+        {
+            bool gpush = false;
+            if (big) {
+                const unsigned bit = 1u << (v & 31);
+                gpush = !(atom_or_release(a.bits_push[(r + 1) & 1] + (v >> 5), bit) & bit);
+            }
+            warp_append(gpush, (unsigned)v, qwork, &a.ctrl->push_ctr[(r + 1) % 3], a.push_items[(r + 1) & 1],
+                        a.push_offs[(r + 1) & 1]);
+        }
+        if (big || !rose) qwork = 0;
+        int qo;
+        const int qtotal = warp_exclusive(qwork, qo);
+        if (qtotal > 0) push_edges<T>(a, r, qbeg, qo, val, 0, qtotal, L);
+        L.relax += qtotal;
+        L.pushes += __popc(__ballot_sync(FULL, qwork > 0));
     }
 }
 
@@ -138,10 +431,8 @@ __device__ void pull_phase(const Args<T> &a, int r, T *red) {
     const int total = (int)(ctr >> 32);
     const int *items = a.pull_items[r & 1];
     const int *offs = a.pull_offs[r & 1];
-    unsigned *bits = a.bits[r & 1];
-    unsigned long long *push_ctr = &a.ctrl->push_ctr[r % 3];
-    int *push_items = a.push_items[r & 1];
-    int *push_offs = a.push_offs[r & 1];
+    unsigned *bits = a.bits_pull[r & 1];
+    unsigned *bits_q = a.bits_push[r & 1];
 
     const int nwarps = gridDim.x * WARPS;
     const int gw = blockIdx.x * WARPS + (threadIdx.x >> 5);
@@ -163,39 +454,8 @@ __device__ void pull_phase(const Args<T> &a, int r, T *red) {
             beg = __ldg(A.row_ptr + v);
         }
         const int stop = min(hi, __shfl_sync(FULL, oend, 31));
-        red[lane] = Cred<T>::TOP;
-        __syncwarp();
-        for (int xb = x; xb < stop; xb += 32) {
-            const int xl = xb + lane;
-            const bool act = xl < stop;
-            int j = 0;
-#pragma unroll
-            for (int s = 16; s >= 1; s >>= 1) {
-                int oj = __shfl_sync(FULL, o, j + s);
-                if (oj <= xl) j += s;
-            }
-            const int bj = __shfl_sync(FULL, beg, j);
-            const int oj = __shfl_sync(FULL, o, j);
-            T t = Cred<T>::TOP;
-            if (act) {
-                const int e = bj + (xl - oj);
-                const int u = __ldg(A.col + e);
-                t = ominus<T>(ld_cg(a.f + u), wmap(__ldg(A.w + e), a.W), a.W.C);
-            }
-            const int key = act ? j : 32 + lane;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                T ov = __shfl_up_sync(FULL, t, d);
-                int ok = __shfl_up_sync(FULL, key, d);
-                if (lane >= d && ok == key) t = min(t, ov);
-            }
-            const int nk = __shfl_down_sync(FULL, key, 1);
-            if (act && (lane == 31 || nk != key)) red[j] = min(red[j], t);
-            __syncwarp();
-        }
+        const T g = pull_min<T>(a, beg, o, x, stop, red);
         // finish the lifts of this window's entries
-        const T g = red[lane];
-        __syncwarp();
         bool changed = false;
         int pwork = 0;
         if (valid && o < stop && oend > x) {
@@ -214,25 +474,26 @@ __device__ void pull_phase(const Args<T> &a, int r, T *red) {
                     atomicExch(a.acc_done + v, 0);
                 }
             }
-            if (done) {
-                const T cur = ld_cg(a.f + v);
-                if (res > cur) {
-                    st_cg(a.f + v, res);
-                    pwork = __ldg(A.rrow_ptr + v + 1) - __ldg(A.rrow_ptr + v);
-                    changed = pwork > 0;
+            if (done && res > ld_cg(a.f + v) && res > atomicMax(a.f + v, res)) {
+                pwork = __ldg(A.rrow_ptr + v + 1) - __ldg(A.rrow_ptr + v);
+                if (pwork > 0) {
+                    const unsigned bit = 1u << (v & 31);
+                    changed = !(ld_cg(bits_q + (v >> 5)) & bit) && !(atomicOr(bits_q + (v >> 5), bit) & bit);
                 }
             }
         }
-        warp_append(changed, (unsigned)v, pwork, push_ctr, push_items, push_offs);
+        warp_append(changed, (unsigned)v, pwork, &a.ctrl->push_ctr[r % 3], a.push_items[r & 1],
+                    a.push_offs[r & 1]);
         x = stop;
         i += 32;
     }
 }
 
 // ---------------------------------------------------------------------------
-// Push phase: send the rises of the push list of round r to predecessors.
+// Push phase: send the rises of the push list of round r to predecessors,
+// then work through the warp's local worklist.
 template <typename T>
-__device__ void push_phase(const Args<T> &a, int r) {
+__device__ void push_phase(const Args<T> &a, int r, T *red, Local<T> &L) {
     const DevArena &A = a.A;
     const int lane = lane_id();
     const unsigned long long ctr = ld_cg(&a.ctrl->push_ctr[r % 3]);
@@ -240,20 +501,14 @@ __device__ void push_phase(const Args<T> &a, int r) {
     const int total = (int)(ctr >> 32);
     const int *items = a.push_items[r & 1];
     const int *offs = a.push_offs[r & 1];
-    unsigned *bits_cur = a.bits[r & 1];
-    unsigned *bits_next = a.bits[(r + 1) & 1];
-    const int nx = (r + 1) % 3;
-    unsigned long long *next_pull_ctr = &a.ctrl->pull_ctr[nx];
-    unsigned long long *next_push_ctr = &a.ctrl->push_ctr[nx];
-    int *next_pull_items = a.pull_items[(r + 1) & 1];
-    int *next_pull_offs = a.pull_offs[(r + 1) & 1];
-    int *next_push_items = a.push_items[(r + 1) & 1];
-    int *next_push_offs = a.push_offs[(r + 1) & 1];
+    unsigned *bits_cur = a.bits_push[r & 1];
 
     const int nwarps = gridDim.x * WARPS;
     const int gw = blockIdx.x * WARPS + (threadIdx.x >> 5);
     const int K = max(32, (total + nwarps - 1) / nwarps);
     const int lo = gw * K;
+    L.top = 0;
+    L.on = a.local_windows > 0;
     if (lo >= total) return;
     const int hi = min(total, lo + K);
 
@@ -265,60 +520,19 @@ __device__ void push_phase(const Args<T> &a, int r) {
         int o = total, oend = total, beg = 0;
         T val = T(0);
         if (valid) {
-            const unsigned raw = (unsigned)ld_cg(items + ii);
-            const int v = (int)(raw & 0x7fffffffu);
+            const int v = ld_cg(items + ii) & 0x7fffffff;
             o = ld_cg(offs + ii);
             oend = ii + 1 < cnt ? ld_cg(offs + ii + 1) : total;
             beg = __ldg(A.rrow_ptr + v);
+            if (o >= lo && o < hi) atomicAnd(bits_cur + (v >> 5), ~(1u << (v & 31)));  // consumed
             val = ld_cg(a.f + v);
-            if ((raw & P1_FLAG) && o >= lo && o < hi) atomicAnd(bits_cur + (v >> 5), ~(1u << (v & 31)));
         }
         const int stop = min(hi, __shfl_sync(FULL, oend, 31));
-        for (int xb = x; xb < stop; xb += 32) {
-            const int xl = xb + lane;
-            const bool act = xl < stop;
-            int j = 0;
-#pragma unroll
-            for (int s = 16; s >= 1; s >>= 1) {
-                int oj = __shfl_sync(FULL, o, j + s);
-                if (oj <= xl) j += s;
-            }
-            const int bj = __shfl_sync(FULL, beg, j);
-            const int oj = __shfl_sync(FULL, o, j);
-            const T vj = __shfl_sync(FULL, val, j);
-            bool want_pull = false, want_push = false;
-            int p = 0, work = 0;
-            if (act) {
-                const int e = bj + (xl - oj);
-                const unsigned pr = __ldg(A.rcol + e);
-                p = (int)(pr & 0x7fffffffu);
-                const T t = ominus<T>(vj, wmap(__ldg(A.rw + e), a.W), a.W.C);
-                bool rose = false;
-                if (pr & P1_FLAG) {
-                    if (t > ld_cg(a.f + p)) rose = t > atomicMax(a.f + p, t);
-                    if (rose) {
-                        work = __ldg(A.rrow_ptr + p + 1) - __ldg(A.rrow_ptr + p);
-                        rose = work > 0;
-                    }
-                } else {
-                    rose = t > ld_cg(a.f + p);
-                    if (rose) work = __ldg(A.row_ptr + p + 1) - __ldg(A.row_ptr + p);
-                }
-                if (rose) {
-                    const unsigned bit = 1u << (p & 31);
-                    unsigned *wd = bits_next + (p >> 5);
-                    if (!(ld_cg(wd) & bit) && !(atomicOr(wd, bit) & bit)) {
-                        want_push = (pr & P1_FLAG) != 0;
-                        want_pull = !want_push;
-                    }
-                }
-            }
-            warp_append(want_pull, (unsigned)p, work, next_pull_ctr, next_pull_items, next_pull_offs);
-            warp_append(want_push, (unsigned)p | P1_FLAG, work, next_push_ctr, next_push_items, next_push_offs);
-        }
+        push_edges<T>(a, r, beg, o, val, x, stop, L);
         x = stop;
         i += 32;
     }
+    drain_local<T>(a, r, red, L);
 }
 
 // ---------------------------------------------------------------------------
@@ -326,7 +540,14 @@ __device__ void push_phase(const Args<T> &a, int r) {
 template <typename T>
 __global__ void __launch_bounds__(THREADS) k_fixpoint(Args<T> a) {
     __shared__ T red_all[WARPS][32];
-    T *red = red_all[threadIdx.x >> 5];
+    __shared__ int stack_all[WARPS][LOCAL_CAP];
+    const int wid = threadIdx.x >> 5;
+    T *red = red_all[wid];
+    Local<T> L;
+    L.stack = stack_all[wid];
+    L.top = 0;
+    L.on = false;
+    L.relax = L.lifts = L.pushes = 0;
     Ctrl *c = a.ctrl;
     unsigned gen = 0;
     for (int r = 0;; ++r) {
@@ -344,7 +565,7 @@ __global__ void __launch_bounds__(THREADS) k_fixpoint(Args<T> a) {
             if (!grid_barrier(c, gridDim.x, gen, BARRIER_LIMIT_NS)) break;
         }
         const unsigned long long qc = ld_cg(&c->push_ctr[r % 3]);
-        push_phase<T>(a, r);
+        push_phase<T>(a, r, red, L);
         if (!grid_barrier(c, gridDim.x, gen, BARRIER_LIMIT_NS)) break;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             c->rounds += 1;
@@ -356,6 +577,11 @@ __global__ void __launch_bounds__(THREADS) k_fixpoint(Args<T> a) {
         const unsigned long long nq = ld_cg(&c->push_ctr[(r + 1) % 3]);
         if (blockIdx.x == 0 && threadIdx.x == 0) c->enqueues += (np & 0xffffffffu) + (nq & 0xffffffffu);
         if ((np & 0xffffffffu) == 0 && (nq & 0xffffffffu) == 0) break;
+    }
+    if (lane_id() == 0 && (L.relax | L.lifts | L.pushes)) {
+        atomicAdd(&c->relax, L.relax);
+        atomicAdd(&c->lifts, L.lifts);
+        atomicAdd(&c->pushes, L.pushes);
     }
 }
 
@@ -413,8 +639,8 @@ static eg_status ensure_state(eg_arena *ar, int bits) {
     size_t o_f = off; off = align_up(off + n * cs);
     size_t o_list[8];
     for (int k = 0; k < 8; ++k) { o_list[k] = off; off = align_up(off + n * 4); }
-    size_t o_bits[2];
-    for (int k = 0; k < 2; ++k) { o_bits[k] = off; off = align_up(off + words * 4); }
+    size_t o_bits[5];
+    for (int k = 0; k < 5; ++k) { o_bits[k] = off; off = align_up(off + words * 4); }
     size_t o_acc = off; off = align_up(off + n * cs);
     size_t o_done = off; off = align_up(off + n * 4);
     size_t o_ctrl = off; off = align_up(off + sizeof(Ctrl));
@@ -430,8 +656,10 @@ static eg_status ensure_state(eg_arena *ar, int bits) {
         sb.d.pull_offs[k] = (int *)(blk + o_list[4 * k + 1]);
         sb.d.push_items[k] = (int *)(blk + o_list[4 * k + 2]);
         sb.d.push_offs[k] = (int *)(blk + o_list[4 * k + 3]);
-        sb.d.bits[k] = (unsigned *)(blk + o_bits[k]);
+        sb.d.bits_pull[k] = (unsigned *)(blk + o_bits[k]);
+        sb.d.bits_push[k] = (unsigned *)(blk + o_bits[2 + k]);
     }
+    sb.d.seed_bits = (unsigned *)(blk + o_bits[4]);
     sb.d.acc = blk + o_acc;
     sb.d.acc_done = (int *)(blk + o_done);
     sb.d.ctrl = (Ctrl *)(blk + o_ctrl);
@@ -446,8 +674,10 @@ static eg_status launch_solve(eg_arena *ar, StateBuffers &sb, const WeightView &
     if (sb.dirty) {
         k_fill<T><<<sms * 4, 256, 0, s>>>((T *)sb.d.acc, n, Cred<T>::TOP);
         EG_CUDA_TRY(cudaMemsetAsync(sb.d.acc_done, 0, (size_t)n * 4, s));
-        EG_CUDA_TRY(cudaMemsetAsync(sb.d.bits[0], 0, ((size_t)n + 31) / 32 * 4, s));
-        EG_CUDA_TRY(cudaMemsetAsync(sb.d.bits[1], 0, ((size_t)n + 31) / 32 * 4, s));
+        for (int k = 0; k < 2; ++k) {
+            EG_CUDA_TRY(cudaMemsetAsync(sb.d.bits_pull[k], 0, ((size_t)n + 31) / 32 * 4, s));
+            EG_CUDA_TRY(cudaMemsetAsync(sb.d.bits_push[k], 0, ((size_t)n + 31) / 32 * 4, s));
+        }
         sb.dirty = false;
     }
     EG_CUDA_TRY(cudaMemsetAsync(sb.d.ctrl, 0, sizeof(Ctrl), s));
@@ -460,14 +690,25 @@ static eg_status launch_solve(eg_arena *ar, StateBuffers &sb, const WeightView &
         a.pull_offs[k] = sb.d.pull_offs[k];
         a.push_items[k] = sb.d.push_items[k];
         a.push_offs[k] = sb.d.push_offs[k];
-        a.bits[k] = sb.d.bits[k];
+        a.bits_pull[k] = sb.d.bits_pull[k];
+        a.bits_push[k] = sb.d.bits_push[k];
     }
     a.acc = (T *)sb.d.acc;
     a.acc_done = sb.d.acc_done;
     a.ctrl = sb.d.ctrl;
     a.max_rounds = max_rounds;
+    a.local_windows = ar->local_windows;
+    a.local_maxdeg = ar->local_maxdeg;
 
     EG_CUDA_TRY(cudaEventRecord(ar->ev0, s));
+    a.seed_bits = nullptr;
+    if (ar->warm_start) {
+        EG_CUDA_TRY(cudaMemsetAsync(sb.d.seed_bits, 0, ((size_t)n + 31) / 32 * 4, s));
+        const int sblocks = (int)std::min<long long>(((long long)n + 7) / 8, (long long)sms * 32);
+        k_seed<<<sblocks, 256, 0, s>>>(ar->d, W, ar->seed_max_pairs, sb.d.seed_bits, &sb.d.ctrl->seeded);
+        EG_CUDA_TRY(cudaGetLastError());
+        a.seed_bits = sb.d.seed_bits;
+    }
     const int init_blocks = (int)std::min<long long>((n + THREADS - 1) / THREADS, (long long)sms * 16);
     k_init<T><<<init_blocks, THREADS, 0, s>>>(a);
     EG_CUDA_TRY(cudaGetLastError());
@@ -555,6 +796,7 @@ eg_status solve(eg_arena *ar, int credit_bits, long long scale, long long shift,
     }
     if (st) {
         st->C = C;
+        st->seeded = (int64_t)hc->seeded;
         st->credit_bits = bits;
         st->status = result;
         st->rounds = (int64_t)hc->rounds;

@@ -36,7 +36,7 @@ STATUS_NAMES = {0: "EG_OK", 1: "EG_PENDING", -1: "EG_ERR_INVALID", -2: "EG_ERR_N
 
 
 class eg_stats(ctypes.Structure):
-    _fields_ = [("C", ctypes.c_int64), ("credit_bits", ctypes.c_int32), ("status", ctypes.c_int32),
+    _fields_ = [("C", ctypes.c_int64), ("seeded", ctypes.c_int64), ("credit_bits", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("rounds", ctypes.c_int64), ("lifts", ctypes.c_int64), ("pushes", ctypes.c_int64),
                 ("relaxations", ctypes.c_int64), ("enqueues", ctypes.c_int64), ("ms", ctypes.c_double),
                 ("fixpoint_ms", ctypes.c_double)]
@@ -60,6 +60,7 @@ SIGNATURES = {
     "eg_destroy": (_I32, [_P]),
     "eg_bound": (_I32, [_P, _I64, _I64, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "eg_solve_credit": (_I32, [_P, _I32, _I64, _I64, _P, ctypes.POINTER(eg_stats), _P, _I64]),
+    "eg_set_option": (_I32, [_P, _I32, _I64]),
     "eg_last_error": (ctypes.c_char_p, []),
     "eg_version": (ctypes.c_char_p, []),
 }
@@ -131,6 +132,16 @@ def eg_bound(arena, w_scale: int = 1, w_shift: int = 0) -> tuple[int, int]:
     return C.value, wm.value
 
 
+EG_OPT_LOCAL_WINDOWS = 1
+EG_OPT_LOCAL_MAXDEG = 2
+EG_OPT_WARM_START = 3
+EG_OPT_SEED_MAX_PAIRS = 4
+
+
+def eg_set_option(arena, option: int, value: int) -> None:
+    _check(load().eg_set_option(arena, option, value))
+
+
 def eg_solve_credit(arena, credit_bits, w_scale, w_shift, credits_out, stream=None, max_rounds=0,
                     raise_on_error=True):
     """credits_out: numpy array (host) or device address / tensor of the
@@ -164,6 +175,12 @@ class Arena:
         out = np.empty(self.n, dtype=np.int32 if credit_bits == 32 else np.int64)
         _, st = eg_solve_credit(self.handle, credit_bits, w_scale, w_shift, out, stream, max_rounds)
         return out, st
+
+    def tune(self, local_windows=None, local_maxdeg=None, warm_start=None, seed_max_pairs=None):
+        for opt, val in ((EG_OPT_LOCAL_WINDOWS, local_windows), (EG_OPT_LOCAL_MAXDEG, local_maxdeg),
+                         (EG_OPT_WARM_START, warm_start), (EG_OPT_SEED_MAX_PAIRS, seed_max_pairs)):
+            if val is not None:
+                eg_set_option(self.handle, opt, int(val))
 
     def bound(self, w_scale=1, w_shift=0):
         return eg_bound(self.handle, w_scale, w_shift)
