@@ -149,6 +149,8 @@ eg_status eg_solve_credit(eg_arena *arena, int32_t credit_bits, int64_t w_scale,
  *     unchanged.  0 starts from f = 0 everywhere, as the paper does.
  *   EG_OPT_SEED_MAX_PAIRS (default 4096): the warm start skips a vertex
  *     whose out-degree times in-degree exceeds this.
+ *   EG_OPT_GRAPH (default 1): batched solves (eg_plan_run) replay a captured
+ *     CUDA graph; 0 launches the kernels directly every run.
  *
  * EG_ERR_INVALID for an unknown option or a negative value.
  */
@@ -156,7 +158,45 @@ eg_status eg_solve_credit(eg_arena *arena, int32_t credit_bits, int64_t w_scale,
 #define EG_OPT_LOCAL_MAXDEG 2
 #define EG_OPT_WARM_START 3
 #define EG_OPT_SEED_MAX_PAIRS 4
+#define EG_OPT_GRAPH 5
 eg_status eg_set_option(eg_arena *arena, int32_t option, int64_t value);
+
+/*
+ * eg_set_parts -- declare the arena a disjoint union of `parts` games: game k
+ * owns vertices [part_ptr[k], part_ptr[k+1]) (host array of parts + 1
+ * offsets, part_ptr[0] = 0, non-decreasing, part_ptr[parts] = n, no empty
+ * part).  Every edge must stay inside its game (EG_ERR_INVALID otherwise).
+ * Used by batched solves (eg_plan_create); a plain arena is one part.
+ */
+eg_status eg_set_parts(eg_arena *arena, int32_t parts, const int64_t *part_ptr);
+
+/*
+ * Batched solves.  A plan solves `count` instances in one persistent launch:
+ * instance i is game part[i] of the arena (or game i if part is NULL) under
+ * the weight map w' = w_scale[i] * w - w_shift[i] (1 and 0 if the arrays
+ * are NULL).  Instances may repeat a game -- many mean-payoff threshold
+ * queries on one arena (Sec. 3, energy / mean-payoff reduction) keep one
+ * copy of the arena and one credit array per query.  Each instance gets its
+ * own bound C (Sec. 3.1) and its own credit range; the result of every
+ * instance equals eg_solve_credit on that game and map alone.
+ *
+ * credit_bits: 32 -> int32 credits out (EG_ERR_OVERFLOW unless every
+ * instance fits, see eg_solve_credit); 64 or 0 -> int64 out.  The plan
+ * computes in int32 when every instance fits and credit_bits != 64.
+ * eg_plan_create computes the bounds and allocates the solve state
+ * (synchronous).  eg_plan_run replays the solve -- warm start, init and the
+ * fixpoint kernel, captured once as a CUDA graph -- and writes instance i's
+ * credits at element offset i_off (eg_plan_instance) of credits_out (host
+ * or device, caller-owned, total elements = sum of the instances' n).
+ * Synchronous; one run at a time per plan; the arena must outlive the plan.
+ */
+typedef struct eg_plan eg_plan;
+eg_status eg_plan_create(eg_arena *arena, int32_t count, const int32_t *part, const int64_t *w_scale,
+                         const int64_t *w_shift, int32_t credit_bits, eg_plan **out);
+/* offset (elements), n, C and the width (32/64) the instance alone would need; any may be NULL */
+eg_status eg_plan_instance(eg_plan *plan, int32_t i, int64_t *offset, int64_t *n, int64_t *C, int32_t *bits);
+eg_status eg_plan_run(eg_plan *plan, void *credits_out, eg_stats *st, void *cuda_stream, int64_t max_rounds);
+eg_status eg_plan_destroy(eg_plan *plan);
 
 /* eg_last_error -- message of the calling thread's last failure ("" if none). */
 const char *eg_last_error(void);

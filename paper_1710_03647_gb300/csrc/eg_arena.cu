@@ -58,6 +58,10 @@ __global__ void k_check_cols(const int *col, int m, int n, unsigned *flags, unsi
 }
 
 // in-degree counts into cnt[0..n-1] (cnt zeroed by the caller)
+__global__ void k_fill_int(int *p, int n, int v) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = v;
+}
+
 __global__ void k_count_in(const int *col, int m, int *cnt) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += gridDim.x * blockDim.x)
         atomicAdd(cnt + col[e], 1);
@@ -113,21 +117,97 @@ static cudaError_t exclusive_scan(int *data, int len, int *scratch, cudaStream_t
     return cudaGetLastError();
 }
 
-// One warp per vertex scatters its out-edges into the reverse CSR.
-__global__ void k_scatter(int n, const int *row_ptr, const int *col, const int *w, const unsigned *owner_bits,
-                          int *fill, unsigned *rcol, int *rw) {
-    const int lane = threadIdx.x & 31;
-    const int nw = gridDim.x * (blockDim.x >> 5);
-    for (int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n; v += nw) {
-        const unsigned tag = (unsigned)v | ((((owner_bits[v >> 5] >> (v & 31)) & 1u) != 0) ? P1_FLAG : 0u);
-        const int b = row_ptr[v], e = row_ptr[v + 1];
-        for (int k = b + lane; k < e; k += 32) {
-            const int u = col[k];
-            const int slot = atomicAdd(fill + u, 1);
-            rcol[slot] = tag;
-            rw[slot] = w[k];
+// Row work is split by degree so that hubs do not serialise: tier 0 gives a
+// row of at most TIER0 edges to one thread, tier 1 a row of at most TIER1
+// edges to one warp, tier 2 a longer row to a whole block.  Each tiered
+// kernel visits every row and skips the rows of the other tiers.
+constexpr int TIER0 = 16;
+constexpr int TIER1 = 2048;
+
+__device__ __forceinline__ int row_tier(int deg) { return deg <= TIER0 ? 0 : (deg <= TIER1 ? 1 : 2); }
+
+// Scatter of one out-edge k of row v into the reverse CSR.
+__device__ __forceinline__ void scatter_edge(int k, unsigned tag, const int *col, const int *w, int *fill,
+                                             unsigned *rcol, int *rw) {
+    const int slot = atomicAdd(fill + col[k], 1);
+    rcol[slot] = tag;
+    rw[slot] = w[k];
+}
+
+__device__ __forceinline__ unsigned owner_tag(const unsigned *owner_bits, int v) {
+    return (unsigned)v | ((((owner_bits[v >> 5] >> (v & 31)) & 1u) != 0) ? P1_FLAG : 0u);
+}
+
+// Tiered row loop: tier 0 gives each thread one row; tiers 1 and 2 first
+// collect the rows of their tier from a chunk of blockDim.x rows into shared
+// memory, then give each collected row to a warp (tier 1) or to the whole
+// block (tier 2).  fn(v, begin, step) visits edges begin, begin+step, ...
+template <typename F>
+__device__ __forceinline__ void for_rows_of_tier(int n, const int *row_ptr, int tier, F fn) {
+    __shared__ int rows[1024];
+    __shared__ int nrows;
+    if (tier == 0) {
+        for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+            const int b = row_ptr[v], e = row_ptr[v + 1];
+            if (row_tier(e - b) == 0) fn(v, b, e, 0, 1);
         }
+        return;
     }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        if (threadIdx.x == 0) nrows = 0;
+        __syncthreads();
+        const int v = base + threadIdx.x;
+        if (v < n && row_tier(row_ptr[v + 1] - row_ptr[v]) == tier) rows[atomicAdd(&nrows, 1)] = v;
+        __syncthreads();
+        const int cnt = nrows;
+        if (tier == 1) {
+            for (int k = wid; k < cnt; k += nwarp) {
+                const int u = rows[k];
+                fn(u, row_ptr[u], row_ptr[u + 1], lane, 32);
+            }
+        } else {
+            for (int k = 0; k < cnt; ++k) {
+                const int u = rows[k];
+                fn(u, row_ptr[u], row_ptr[u + 1], (int)threadIdx.x, (int)blockDim.x);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_scatter(int n, const int *row_ptr, const int *col, const int *w, const unsigned *owner_bits,
+                          int *fill, unsigned *rcol, int *rw, int tier) {
+    for_rows_of_tier(n, row_ptr, tier, [&](int v, int b, int e, int first, int step) {
+        const unsigned tag = owner_tag(owner_bits, v);
+        for (int k = b + first; k < e; k += step) scatter_edge(k, tag, col, w, fill, rcol, rw);
+    });
+}
+
+// Smallest and largest weight of every row (rows are never empty here).
+// Tier 0 writes directly; tiers 1 and 2 combine with atomics on outputs that
+// start at (INT_MAX, INT_MIN).
+__global__ void k_row_extremes(int n, const int *row_ptr, const int *w, int *wmin, int *wmax, int tier) {
+    for_rows_of_tier(n, row_ptr, tier, [&](int v, int b, int e, int first, int step) {
+        int lo = 0x7fffffff, hi = (int)0x80000000;
+        for (int k = b + first; k < e; k += step) {
+            lo = min(lo, w[k]);
+            hi = max(hi, w[k]);
+        }
+        if (step == 1) {
+            wmin[v] = lo;
+            wmax[v] = hi;
+            return;
+        }
+        for (int d = 16; d; d >>= 1) {
+            lo = min(lo, __shfl_xor_sync(FULL, lo, d));
+            hi = max(hi, __shfl_xor_sync(FULL, hi, d));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(wmin + v, lo);
+            atomicMax(wmax + v, hi);
+        }
+    });
 }
 
 // Tags caller-provided reverse columns with the owner bit of the predecessor.
@@ -260,6 +340,8 @@ static eg_status create(int64_t n64, int64_t m64, const int64_t *row_ptr, const 
         const size_t o_rcol = off; off = align_up(off + (size_t)m * 4);
         const size_t o_rw = off; off = align_up(off + (size_t)m * 4);
         const size_t o_own = off; off = align_up(off + words * 4);
+        const size_t o_wmin = off; off = align_up(off + (size_t)n * 4);
+        const size_t o_wmax = off; off = align_up(off + (size_t)n * 4);
         char *blk = nullptr;
         unsigned *hflags = nullptr;
         unsigned long long hh[2] = {0, 0};
@@ -273,6 +355,8 @@ static eg_status create(int64_t n64, int64_t m64, const int64_t *row_ptr, const 
         unsigned *drcol = (unsigned *)(blk + o_rcol);
         int *drw = (int *)(blk + o_rw);
         unsigned *down = (unsigned *)(blk + o_own);
+        int *dwmin = (int *)(blk + o_wmin);
+        int *dwmax = (int *)(blk + o_wmax);
         // temporaries: int64 offsets (x2), flags, hashes, scan scratch, fill pointers
         size_t t = 0;
         const size_t t_rp = t; t = align_up(t + ((size_t)n + 1) * 8);
@@ -334,8 +418,11 @@ static eg_status create(int64_t n64, int64_t m64, const int64_t *row_ptr, const 
                 TRY(cudaGetLastError());
                 TRY(exclusive_scan(rrp32, n + 1, scan_scratch, s));
                 TRY(cudaMemcpyAsync(fill, rrp32, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
-                const int gw = (int)std::min<long long>(((long long)n + 7) / 8, 1 << 16);
-                k_scatter<<<gw, 256, 0, s>>>(n, rp32, dcol, dw, down, fill, drcol, drw);
+                const int gt = (int)std::min<long long>(((long long)n + 255) / 256, 1 << 14);
+                const int gw = (int)std::min<long long>(((long long)n + 7) / 8, 1 << 14);
+                k_scatter<<<gt, 256, 0, s>>>(n, rp32, dcol, dw, down, fill, drcol, drw, 0);
+                k_scatter<<<gt, 256, 0, s>>>(n, rp32, dcol, dw, down, fill, drcol, drw, 1);
+                k_scatter<<<gt, 256, 0, s>>>(n, rp32, dcol, dw, down, fill, drcol, drw, 2);
                 TRY(cudaGetLastError());
             } else {
                 const int gw = (int)std::min<long long>(((long long)n + 7) / 8, 1 << 16);
@@ -344,6 +431,16 @@ static eg_status create(int64_t n64, int64_t m64, const int64_t *row_ptr, const 
                 k_tag_rcol<<<ge, 256, 0, s>>>(m, down, drcol);
                 TRY(cudaGetLastError());
                 TRY(cudaMemcpyAsync(hh, dhash, 16, cudaMemcpyDeviceToHost, s));
+            }
+            {
+                const int gt = (int)std::min<long long>(((long long)n + 255) / 256, 1 << 14);
+                const int gw = (int)std::min<long long>(((long long)n + 7) / 8, 1 << 14);
+                k_fill_int<<<gt, 256, 0, s>>>(dwmin, n, 0x7fffffff);
+                k_fill_int<<<gt, 256, 0, s>>>(dwmax, n, (int)0x80000000);
+                k_row_extremes<<<gt, 256, 0, s>>>(n, rp32, dw, dwmin, dwmax, 0);
+                k_row_extremes<<<gt, 256, 0, s>>>(n, rp32, dw, dwmin, dwmax, 1);
+                k_row_extremes<<<gt, 256, 0, s>>>(n, rp32, dw, dwmin, dwmax, 2);
+                TRY(cudaGetLastError());
             }
             TRY(cudaStreamSynchronize(s));
             cudaFree(tmp);
@@ -363,6 +460,8 @@ static eg_status create(int64_t n64, int64_t m64, const int64_t *row_ptr, const 
         a->d.rcol = drcol;
         a->d.rw = drw;
         a->d.owner_bits = down;
+        a->d.wmin = dwmin;
+        a->d.wmax = dwmax;
         TRY(cudaEventCreate(&a->ev0));
         TRY(cudaEventCreate(&a->ev1));
         TRY(cudaEventCreate(&a->evk));
@@ -431,6 +530,72 @@ eg_status eg_solve_credit(eg_arena *arena, int32_t credit_bits, int64_t w_scale,
     }
 }
 
+}  // extern "C"
+
+namespace eg {
+// Every edge of vertex v (one warp per vertex) must stay in v's game.
+__global__ void k_check_parts(int n, const int *row_ptr, const int *col, const long long *pp, int parts,
+                              unsigned *bad) {
+    const int lane = threadIdx.x & 31, nw = gridDim.x * (blockDim.x >> 5);
+    for (int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n; v += nw) {
+        int lo = 0, hi = parts;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (pp[mid] <= v) lo = mid;
+            else hi = mid;
+        }
+        const long long a = pp[lo], b = pp[lo + 1];
+        for (int k = row_ptr[v] + lane; k < row_ptr[v + 1]; k += 32)
+            if (col[k] < a || col[k] >= b) atomicOr(bad, 1u);
+    }
+}
+}  // namespace eg
+
+extern "C" {
+
+eg_status eg_set_parts(eg_arena *arena, int32_t parts, const int64_t *part_ptr) {
+    eg::clear_error();
+    if (!arena || parts < 1 || !part_ptr) {
+        eg::set_error("need an arena, parts >= 1 and part_ptr");
+        return EG_ERR_INVALID;
+    }
+    if (part_ptr[0] != 0 || part_ptr[parts] != arena->n) {
+        eg::set_error("part_ptr must start at 0 and end at n");
+        return EG_ERR_INVALID;
+    }
+    for (int k = 0; k < parts; ++k)
+        if (part_ptr[k + 1] <= part_ptr[k]) {
+            eg::set_error("part %d is empty or offsets decrease", k);
+            return EG_ERR_INVALID;
+        }
+    long long *dpp = nullptr;
+    unsigned *dbad = nullptr;
+    unsigned hbad = 0;
+    eg_status rc = EG_OK;
+    if (cudaMalloc((void **)&dpp, ((size_t)parts + 1) * 8) != cudaSuccess ||
+        cudaMalloc((void **)&dbad, 4) != cudaSuccess) {
+        eg::set_error("device allocation failed");
+        rc = EG_ERR_OOM;
+    } else {
+        cudaMemcpy(dpp, part_ptr, ((size_t)parts + 1) * 8, cudaMemcpyHostToDevice);
+        cudaMemset(dbad, 0, 4);
+        const int gw = (int)std::min<long long>(((long long)arena->n + 7) / 8, 1 << 14);
+        eg::k_check_parts<<<gw, 256>>>(arena->n, arena->d.row_ptr, arena->d.col, dpp, parts, dbad);
+        cudaError_t e = cudaMemcpy(&hbad, dbad, 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            eg::set_error("part check failed: %s", cudaGetErrorString(e));
+            rc = EG_ERR_CUDA;
+        } else if (hbad) {
+            eg::set_error("an edge leaves its game");
+            rc = EG_ERR_INVALID;
+        }
+    }
+    if (dpp) cudaFree(dpp);
+    if (dbad) cudaFree(dbad);
+    if (rc == EG_OK) arena->part_ptr.assign(part_ptr, part_ptr + parts + 1);
+    return rc;
+}
+
 eg_status eg_set_option(eg_arena *arena, int32_t option, int64_t value) {
     eg::clear_error();
     if (!arena) {
@@ -452,6 +617,13 @@ eg_status eg_set_option(eg_arena *arena, int32_t option, int64_t value) {
         arena->warm_start = (int)value;
         break;
     case EG_OPT_SEED_MAX_PAIRS: arena->seed_max_pairs = value; break;
+    case EG_OPT_GRAPH:
+        if (value > 1) {
+            eg::set_error("EG_OPT_GRAPH takes 0 or 1");
+            return EG_ERR_INVALID;
+        }
+        arena->use_graph = (int)value;
+        break;
     default: eg::set_error("unknown option %d", option); return EG_ERR_INVALID;
     }
     return EG_OK;

@@ -30,6 +30,16 @@ template <> struct Cred<long long> {
 // w' = scale * w - shift (the weight view of a threshold query)
 __device__ __forceinline__ long long wmap(int w, const WeightView &v) { return v.scale * (long long)w - v.shift; }
 
+// Extremes of w' = scale * w - shift over a vertex's out-edges, from the
+// extremes of its raw weights (the map is monotone: increasing for
+// scale >= 0, decreasing otherwise).
+__device__ __forceinline__ long long wmap_min(int wmin, int wmax, const WeightView &v) {
+    return v.scale >= 0 ? wmap(wmin, v) : wmap(wmax, v);
+}
+__device__ __forceinline__ long long wmap_max(int wmin, int wmax, const WeightView &v) {
+    return v.scale >= 0 ? wmap(wmax, v) : wmap(wmin, v);
+}
+
 // a (-) b over {0..C} u {TOP} (Sec. 3.1, bounded by the codomain C_G):
 // TOP stays TOP, a value above C becomes TOP, a negative one becomes 0.
 template <typename T>

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/eg.h"
 
@@ -48,6 +49,8 @@ struct DevArena {
     const unsigned *rcol;       // m: predecessor id | (owner(pred) is V1) << 31
     const int *rw;              // m: w(pred, v)
     const unsigned *owner_bits; // ceil(n / 32)
+    const int *wmin;            // n: smallest weight on the vertex's out-edges
+    const int *wmax;            // n: largest weight on the vertex's out-edges
 };
 
 // Weight view w' = scale * w - shift and the bound C of that view.
@@ -74,6 +77,7 @@ struct DevState {
 
 struct StateBuffers {
     int bits = 0;      // 0 = not allocated, else 32 / 64
+    long long nf = 0;  // credits the buffers hold
     bool dirty = true; // scratch (acc, acc_done, bitmaps) needs resetting
     DevState d{};
     void *block = nullptr;
@@ -96,6 +100,8 @@ struct eg_arena {
     int local_maxdeg = 64;      // largest degree of a vertex handled through the local worklist
     int warm_start = 1;         // TOP on player-1 negative cycles of length <= 2 before lifting
     long long seed_max_pairs = 4096;
+    int use_graph = 1;                // batched solves replay a captured graph
+    std::vector<long long> part_ptr;  // game boundaries (empty: one game)
 };
 
 namespace eg {

@@ -50,10 +50,24 @@ __device__ __forceinline__ long long xchg(long long *p, long long v) {
     return (long long)atomicExch((unsigned long long *)p, (unsigned long long)v);
 }
 
+// Instances of a batched solve: instance i owns credits [fbase[i], fbase[i+1])
+// and views arena vertices v = g - delta[i] (credit index g) under the map
+// w' = scale[i] * w - shift[i] with bound C[i].
+struct InstTable {
+    int count;
+    const int *fbase;  // count + 1
+    const int *delta;
+    const long long *scale;
+    const long long *shift;
+    const long long *C;
+};
+
 template <typename T>
 struct Args {
     DevArena A;
-    WeightView W;
+    WeightView W;      // the single instance's view (MULTI = false)
+    InstTable I;       // the instances (MULTI = true)
+    int nf;            // credits: n (single) or the sum over instances
     T *f;
     int *pull_items[2];
     int *pull_offs[2];
@@ -70,19 +84,58 @@ struct Args {
     int local_maxdeg;   // largest degree a vertex may have to be chained locally
 };
 
+// One instance's view of the arena, carried per list entry.
+struct View {
+    int delta;
+    long long scale;
+    long long shift;
+    long long C;
+};
+
+__device__ __forceinline__ long long wmapv(int w, const View &v) { return v.scale * (long long)w - v.shift; }
+
+__device__ __forceinline__ int inst_of(const InstTable &I, int g) {
+    int lo = 0, hi = I.count;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(I.fbase + mid) <= g) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <bool MULTI, typename T>
+__device__ __forceinline__ View view_of(const Args<T> &a, int g) {
+    if (!MULTI) return View{0, a.W.scale, a.W.shift, a.W.C};
+    const int i = inst_of(a.I, g);
+    return View{__ldg(a.I.delta + i), __ldg(a.I.scale + i), __ldg(a.I.shift + i), __ldg(a.I.C + i)};
+}
+
+// View of a lane that holds no entry.  It must still be the instance's view
+// when there is one instance: such a lane processes edges of other lanes'
+// entries, and with one instance views are not exchanged between lanes.
+template <bool MULTI, typename T>
+__device__ __forceinline__ View idle_view(const Args<T> &a) {
+    return MULTI ? View{0, 0, 0, 0} : View{0, a.W.scale, a.W.shift, a.W.C};
+}
+
+template <bool MULTI>
+__device__ __forceinline__ View shfl_view(const View &v, int j) {
+    if (!MULTI) return v;
+    return View{__shfl_sync(FULL, v.delta, j), __shfl_sync(FULL, v.scale, j), __shfl_sync(FULL, v.shift, j),
+                __shfl_sync(FULL, v.C, j)};
+}
+
 // ---------------------------------------------------------------------------
-// Bound C = M_G = sum_v max(0, max_e -w'(e)) and max |w'| (Sec. 3.1).
+// Bound C = M_G = sum_v max(0, max_e -w'(e)) and max |w'| (Sec. 3.1), from the
+// per-vertex extremes of the weights: O(n), coalesced.
 __global__ void k_bound(DevArena A, WeightView W, unsigned long long *out_C, unsigned long long *out_wmax) {
     long long sum = 0, wmax = 0;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < A.n; v += gridDim.x * blockDim.x) {
-        int b = __ldg(A.row_ptr + v), e = __ldg(A.row_ptr + v + 1);
-        long long worst = 0;
-        for (int k = b; k < e; ++k) {
-            long long wv = wmap(__ldg(A.w + k), W);
-            worst = max(worst, -wv);
-            wmax = max(wmax, wv < 0 ? -wv : wv);
-        }
-        sum += worst;
+        const int lo = __ldg(A.wmin + v), hi = __ldg(A.wmax + v);
+        const long long mn = wmap_min(lo, hi, W), mx = wmap_max(lo, hi, W);
+        sum += mn < 0 ? -mn : 0;
+        wmax = max(wmax, max(mn < 0 ? -mn : mn, mx < 0 ? -mx : mx));
     }
     for (int d = 16; d; d >>= 1) {
         sum += __shfl_down_sync(FULL, sum, d);
@@ -107,15 +160,18 @@ __global__ void k_fill(T *p, long long n, T v) {
 // (Lemma "EGcycles" with memoryless determinacy, Sec. 3).  Its least-EPM
 // value is TOP, so starting it at TOP stays below the least fixpoint.
 // Looked for: negative self-loops and 2-cycles u -> t -> u.  One warp per
-// player-1 vertex compares each out-edge (u, t) with each in-edge (s, u)
+// player-1 credit compares each out-edge (u, t) with each in-edge (s, u)
 // for s == t; vertices with out-degree x in-degree above max_pairs are
 // skipped (the warm start is optional, missing a cycle only costs time).
-__global__ void k_seed(DevArena A, WeightView W, long long max_pairs, unsigned *seed_bits,
-                       unsigned long long *count) {
+template <bool MULTI, typename T>
+__global__ void k_seed(Args<T> a, long long max_pairs, unsigned *seed_bits, unsigned long long *count) {
+    const DevArena &A = a.A;
     const int lane = lane_id();
     const int nw = gridDim.x * (blockDim.x >> 5);
     unsigned found_total = 0;
-    for (int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < A.n; u += nw) {
+    for (int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < a.nf; g += nw) {
+        const View vw = view_of<MULTI>(a, g);
+        const int u = g - vw.delta;
         if (!((__ldg(A.owner_bits + (u >> 5)) >> (u & 31)) & 1u)) continue;
         const int ob = __ldg(A.row_ptr + u), oe = __ldg(A.row_ptr + u + 1);
         const int ib = __ldg(A.rrow_ptr + u), ie = __ldg(A.rrow_ptr + u + 1);
@@ -127,7 +183,7 @@ __global__ void k_seed(DevArena A, WeightView W, long long max_pairs, unsigned *
             long long wt = 0;
             if (k < oe) {
                 t = __ldg(A.col + k);
-                wt = wmap(__ldg(A.w + k), W);
+                wt = wmapv(__ldg(A.w + k), vw);
                 if (t == u && wt < 0) found = true;  // negative self-loop
             }
             for (int jb = ib; jb < ie; jb += 32) {
@@ -136,7 +192,7 @@ __global__ void k_seed(DevArena A, WeightView W, long long max_pairs, unsigned *
                 long long ws = 0;
                 if (j < ie) {
                     sv = __ldg(A.rcol + j);
-                    ws = wmap(__ldg(A.rw + j), W);
+                    ws = wmapv(__ldg(A.rw + j), vw);
                 }
                 const int cnt = min(32, ie - jb);
                 for (int q = 0; q < cnt; ++q) {
@@ -149,7 +205,7 @@ __global__ void k_seed(DevArena A, WeightView W, long long max_pairs, unsigned *
             }
         }
         if (__any_sync(FULL, found)) {
-            if (lane == 0) atomicOr(seed_bits + (u >> 5), 1u << (u & 31));
+            if (lane == 0) atomicOr(seed_bits + (g >> 5), 1u << (g & 31));
             ++found_total;
         }
     }
@@ -158,37 +214,74 @@ __global__ void k_seed(DevArena A, WeightView W, long long max_pairs, unsigned *
 
 // ---------------------------------------------------------------------------
 // Initialisation (Algorithm 3, lines 1-3, with the first lift folded in):
-// f(v) = delta(0, v)(v), i.e. max(0, -w') maximised (V1) or minimised (V0)
-// over v's edges.  That is positive exactly for the initial set L of
-// Algorithm 1 (V0 with every edge negative, V1 with some edge negative);
-// those vertices enter push list 0.
-template <typename T>
+// f(v) = delta(0, v)(v).  With every successor at 0 that is max(0, -w') taken
+// at the smallest w' of v's edges for a player-1 vertex (max over edges) and
+// at the largest for a player-0 vertex (min over edges), so it needs only the
+// per-vertex weight extremes.  It is positive exactly for the initial set L of
+// Algorithm 1 (V0 with every edge negative, V1 with some edge negative); those
+// vertices, and the warm-start ones (TOP), enter push list 0.
+template <bool MULTI, typename T>
 __global__ void __launch_bounds__(THREADS) k_init(Args<T> a) {
     const DevArena &A = a.A;
     const int nthreads = gridDim.x * blockDim.x;
-    for (int base = blockIdx.x * blockDim.x; base < A.n; base += nthreads) {
-        int v = base + threadIdx.x;
+    for (int base = blockIdx.x * blockDim.x; base < a.nf; base += nthreads) {
+        const int g = base + threadIdx.x;
         bool want = false;
         int work = 0;
-        unsigned item = 0;
-        if (v < A.n) {
+        if (g < a.nf) {
+            const View vw = view_of<MULTI>(a, g);
+            const int v = g - vw.delta;
             const bool p1 = (__ldg(A.owner_bits + (v >> 5)) >> (v & 31)) & 1u;
-            const int b = __ldg(A.row_ptr + v), e = __ldg(A.row_ptr + v + 1);
-            T g = p1 ? T(0) : Cred<T>::TOP;
-            if (a.seed_bits && ((a.seed_bits[v >> 5] >> (v & 31)) & 1u)) {
-                g = Cred<T>::TOP;
+            T f0;
+            if (a.seed_bits && ((a.seed_bits[g >> 5] >> (g & 31)) & 1u)) {
+                f0 = Cred<T>::TOP;
             } else {
-                for (int k = b; k < e; ++k) {
-                    T t = ominus<T>(T(0), wmap(__ldg(A.w + k), a.W), a.W.C);
-                    g = p1 ? max(g, t) : min(g, t);
-                }
+                const int lo = __ldg(A.wmin + v), hi = __ldg(A.wmax + v);
+                const long long smin = vw.scale >= 0 ? wmapv(lo, vw) : wmapv(hi, vw);
+                const long long smax = vw.scale >= 0 ? wmapv(hi, vw) : wmapv(lo, vw);
+                f0 = ominus<T>(T(0), p1 ? smin : smax, vw.C);
             }
-            a.f[v] = g;
+            a.f[g] = f0;
             work = __ldg(A.rrow_ptr + v + 1) - __ldg(A.rrow_ptr + v);
-            want = g > T(0) && work > 0;
-            item = (unsigned)v | (p1 ? P1_FLAG : 0u);
+            want = f0 > T(0) && work > 0;
         }
-        warp_append(want, item, work, &a.ctrl->push_ctr[0], a.push_items[0], a.push_offs[0]);
+        warp_append(want, (unsigned)g, work, &a.ctrl->push_ctr[0], a.push_items[0], a.push_offs[0]);
+    }
+}
+
+// Per-instance bound C = M_G and max |w'| of every instance (one credit per
+// thread, from the weight extremes of its arena vertex; a warp whose credits
+// all belong to one instance adds them with one atomic).
+__global__ void k_bound_inst(DevArena A, InstTable I, int nf, unsigned long long *C, unsigned long long *wmax) {
+    const int lane = lane_id();
+    for (int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < nf; base += gridDim.x * blockDim.x) {
+        const int g = base + lane;
+        int i = -1;
+        long long def = 0, mag = 0;
+        if (g < nf) {
+            i = inst_of(I, g);
+            const View vw{__ldg(I.delta + i), __ldg(I.scale + i), __ldg(I.shift + i), 0};
+            const int v = g - vw.delta;
+            const int lo = __ldg(A.wmin + v), hi = __ldg(A.wmax + v);
+            const long long a1 = wmapv(lo, vw), a2 = wmapv(hi, vw);
+            const long long mn = min(a1, a2), mx = max(a1, a2);
+            def = mn < 0 ? -mn : 0;
+            mag = max(mn < 0 ? -mn : mn, mx < 0 ? -mx : mx);
+        }
+        const int i0 = __shfl_sync(FULL, i, 0);
+        if (__all_sync(FULL, i == i0)) {
+            for (int d = 16; d; d >>= 1) {
+                def += __shfl_down_sync(FULL, def, d);
+                mag = max(mag, __shfl_down_sync(FULL, mag, d));
+            }
+            if (lane == 0 && i0 >= 0) {
+                atomicAdd(C + i0, (unsigned long long)def);
+                atomicMax(wmax + i0, (unsigned long long)mag);
+            }
+        } else if (i >= 0) {
+            atomicAdd(C + i, (unsigned long long)def);
+            atomicMax(wmax + i, (unsigned long long)mag);
+        }
     }
 }
 
@@ -222,9 +315,9 @@ __device__ __forceinline__ int warp_exclusive(int work, int &excl) {
 }
 
 // Minimum of f(u) (-) w(v,u) over the edges [x0, stop) of the window, per
-// owning lane (TOP for lanes that own none of them).
-template <typename T>
-__device__ __forceinline__ T pull_min(const Args<T> &a, int beg, int o, int x0, int stop, T *red) {
+// owning lane (TOP for lanes that own none of them).  vw: the lane's view.
+template <bool MULTI, typename T>
+__device__ __forceinline__ T pull_min(const Args<T> &a, int beg, int o, const View &vw, int x0, int stop, T *red) {
     const int lane = lane_id();
     red[lane] = Cred<T>::TOP;
     __syncwarp();
@@ -234,11 +327,12 @@ __device__ __forceinline__ T pull_min(const Args<T> &a, int beg, int o, int x0, 
         const int j = owner_lane(o, xl);
         const int bj = __shfl_sync(FULL, beg, j);
         const int oj = __shfl_sync(FULL, o, j);
+        const View vj = shfl_view<MULTI>(vw, j);
         T t = Cred<T>::TOP;
         if (act) {
             const int e = bj + (xl - oj);
-            const int u = __ldg(a.A.col + e);
-            t = ominus<T>(ld_cg(a.f + u), wmap(__ldg(a.A.w + e), a.W), a.W.C);
+            const int u = __ldg(a.A.col + e) + vj.delta;
+            t = ominus<T>(ld_cg(a.f + u), wmapv(__ldg(a.A.w + e), vj), vj.C);
         }
         const int key = act ? j : 32 + lane;
 #pragma unroll
@@ -268,11 +362,11 @@ struct Local {
 
 constexpr unsigned NEED_NONE = 0, NEED_PULL = 1, NEED_PUSH = 2;
 
-// Routes vertices that need work in this or the next round.  NEED_PULL: a
+// Routes credits that need work in this or the next round.  NEED_PULL: a
 // player-0 vertex that may lift; NEED_PUSH: a vertex whose rise must reach
-// its predecessors.  The next round's bitmap of that kind marks a vertex as
+// its predecessors.  The next round's bitmap of that kind marks a credit as
 // queued -- in some warp's local worklist or in the next round's list -- so a
-// vertex already queued absorbs the request (it reads fresh credits when it
+// credit already queued absorbs the request (it reads fresh credits when it
 // is processed).  Newly queued small vertices go to the warp's local
 // worklist while it has room; the rest join the next round's lists.
 template <typename T>
@@ -307,9 +401,9 @@ __device__ __forceinline__ void route(const Args<T> &a, int r, unsigned need, in
 // [x0, stop): t = val (-) w(p, v) for every predecessor p.  A player-1 p takes
 // max(f(p), t) (atomicMax) and, if it rose, needs a push; a player-0 p with
 // f(p) < t may need a lift.
-template <typename T>
-__device__ __forceinline__ void push_edges(const Args<T> &a, int r, int beg, int o, T val, int x0, int stop,
-                                           Local<T> &L) {
+template <bool MULTI, typename T>
+__device__ __forceinline__ void push_edges(const Args<T> &a, int r, int beg, int o, T val, const View &vw, int x0,
+                                           int stop, Local<T> &L) {
     const int lane = lane_id();
     for (int xb = x0; xb < stop; xb += 32) {
         const int xl = xb + lane;
@@ -318,21 +412,23 @@ __device__ __forceinline__ void push_edges(const Args<T> &a, int r, int beg, int
         const int bj = __shfl_sync(FULL, beg, j);
         const int oj = __shfl_sync(FULL, o, j);
         const T vj = __shfl_sync(FULL, val, j);
+        const View wj = shfl_view<MULTI>(vw, j);
         unsigned need = NEED_NONE;
         int p = 0, work = 0;
         if (act) {
             const int e = bj + (xl - oj);
             const unsigned pr = __ldg(a.A.rcol + e);
-            p = (int)(pr & 0x7fffffffu);
-            const T t = ominus<T>(vj, wmap(__ldg(a.A.rw + e), a.W), a.W.C);
+            const int pa = (int)(pr & 0x7fffffffu);
+            p = pa + wj.delta;
+            const T t = ominus<T>(vj, wmapv(__ldg(a.A.rw + e), wj), wj.C);
             if (t > ld_cg(a.f + p)) {
                 if (pr & P1_FLAG) {
                     if (t > atomicMax(a.f + p, t)) {
-                        work = __ldg(a.A.rrow_ptr + p + 1) - __ldg(a.A.rrow_ptr + p);
+                        work = __ldg(a.A.rrow_ptr + pa + 1) - __ldg(a.A.rrow_ptr + pa);
                         if (work > 0) need = NEED_PUSH;
                     }
                 } else {
-                    work = __ldg(a.A.row_ptr + p + 1) - __ldg(a.A.row_ptr + p);
+                    work = __ldg(a.A.row_ptr + pa + 1) - __ldg(a.A.row_ptr + pa);
                     need = NEED_PULL;
                 }
             }
@@ -345,7 +441,7 @@ __device__ __forceinline__ void push_edges(const Args<T> &a, int r, int beg, int
 // lift of its player-0 entries (in place, atomicMax) followed by a push of
 // every entry that rose and of the player-1 entries.  Runs for at most
 // a.local_windows windows, then hands what is left to the next round.
-template <typename T>
+template <bool MULTI, typename T>
 __device__ void drain_local(const Args<T> &a, int r, T *red, Local<T> &L) {
     const int lane = lane_id();
     int windows = 0;
@@ -357,23 +453,26 @@ __device__ void drain_local(const Args<T> &a, int r, T *red, Local<T> &L) {
         const int raw = have ? L.stack[L.top - 1 - lane] : 0;
         __syncwarp();
         L.top -= take;
-        const int v = raw & 0x7fffffff;
+        const int g = raw & 0x7fffffff;
         const bool is_push = have && (raw & (int)P1_FLAG);
         const bool is_pull = have && !(raw & (int)P1_FLAG);
+        View vw = idle_view<MULTI>(a);
+        if (have) vw = view_of<MULTI>(a, g);
+        const int v = g - vw.delta;
         if (!L.on) {  // budget spent: the entries (still marked) join the next round's lists
             const int work = !have ? 0
                              : is_pull ? __ldg(a.A.row_ptr + v + 1) - __ldg(a.A.row_ptr + v)
                                        : __ldg(a.A.rrow_ptr + v + 1) - __ldg(a.A.rrow_ptr + v);
             const int nx = (r + 1) % 3;
-            warp_append(is_pull, (unsigned)v, work, &a.ctrl->pull_ctr[nx], a.pull_items[(r + 1) & 1],
+            warp_append(is_pull, (unsigned)g, work, &a.ctrl->pull_ctr[nx], a.pull_items[(r + 1) & 1],
                         a.pull_offs[(r + 1) & 1]);
-            warp_append(is_push, (unsigned)v, work, &a.ctrl->push_ctr[nx], a.push_items[(r + 1) & 1],
+            warp_append(is_push, (unsigned)g, work, &a.ctrl->push_ctr[nx], a.push_items[(r + 1) & 1],
                         a.push_offs[(r + 1) & 1]);
             continue;
         }
         if (have) {  // unmark before reading credits
             unsigned *bits = is_pull ? a.bits_pull[(r + 1) & 1] : a.bits_push[(r + 1) & 1];
-            atom_and_acquire(bits + (v >> 5), ~(1u << (v & 31)));
+            atom_and_acquire(bits + (g >> 5), ~(1u << (g & 31)));
         }
         // lifts
         int pbeg = 0, pwork = 0;
@@ -383,15 +482,15 @@ __device__ void drain_local(const Args<T> &a, int r, T *red, Local<T> &L) {
         }
         int po;
         const int ptotal = warp_exclusive(pwork, po);
-        T g = Cred<T>::TOP;
-        if (ptotal > 0) g = pull_min<T>(a, pbeg, po, 0, ptotal, red);
+        T gmin = Cred<T>::TOP;
+        if (ptotal > 0) gmin = pull_min<MULTI, T>(a, pbeg, po, vw, 0, ptotal, red);
         bool rose = is_push;
         T val = T(0);
         if (is_pull) {
-            rose = g > atomicMax(a.f + v, g);
-            val = g;
+            rose = gmin > atomicMax(a.f + g, gmin);
+            val = gmin;
         } else if (is_push) {
-            val = ld_cg(a.f + v);
+            val = ld_cg(a.f + g);
         }
         L.relax += ptotal;
         L.lifts += __popc(__ballot_sync(FULL, is_pull));
@@ -405,16 +504,16 @@ __device__ void drain_local(const Args<T> &a, int r, T *red, Local<T> &L) {
         {
             bool gpush = false;
             if (big) {
-                const unsigned bit = 1u << (v & 31);
-                gpush = !(atom_or_release(a.bits_push[(r + 1) & 1] + (v >> 5), bit) & bit);
+                const unsigned bit = 1u << (g & 31);
+                gpush = !(atom_or_release(a.bits_push[(r + 1) & 1] + (g >> 5), bit) & bit);
             }
-            warp_append(gpush, (unsigned)v, qwork, &a.ctrl->push_ctr[(r + 1) % 3], a.push_items[(r + 1) & 1],
+            warp_append(gpush, (unsigned)g, qwork, &a.ctrl->push_ctr[(r + 1) % 3], a.push_items[(r + 1) & 1],
                         a.push_offs[(r + 1) & 1]);
         }
         if (big || !rose) qwork = 0;
         int qo;
         const int qtotal = warp_exclusive(qwork, qo);
-        if (qtotal > 0) push_edges<T>(a, r, qbeg, qo, val, 0, qtotal, L);
+        if (qtotal > 0) push_edges<MULTI, T>(a, r, qbeg, qo, val, vw, 0, qtotal, L);
         L.relax += qtotal;
         L.pushes += __popc(__ballot_sync(FULL, qwork > 0));
     }
@@ -422,7 +521,7 @@ __device__ void drain_local(const Args<T> &a, int r, T *red, Local<T> &L) {
 
 // ---------------------------------------------------------------------------
 // Pull phase: lift the player-0 vertices of the pull list of round r.
-template <typename T>
+template <bool MULTI, typename T>
 __device__ void pull_phase(const Args<T> &a, int r, T *red) {
     const DevArena &A = a.A;
     const int lane = lane_id();
@@ -446,43 +545,46 @@ __device__ void pull_phase(const Args<T> &a, int r, T *red) {
     while (x < hi) {
         const int ii = i + lane;
         const bool valid = ii < cnt;
-        int v = 0, o = total, oend = total, beg = 0;
+        int g = 0, v = 0, o = total, oend = total, beg = 0;
+        View vw = idle_view<MULTI>(a);
         if (valid) {
-            v = ld_cg(items + ii) & 0x7fffffff;
+            g = ld_cg(items + ii) & 0x7fffffff;
+            vw = view_of<MULTI>(a, g);
+            v = g - vw.delta;
             o = ld_cg(offs + ii);
             oend = ii + 1 < cnt ? ld_cg(offs + ii + 1) : total;
             beg = __ldg(A.row_ptr + v);
         }
         const int stop = min(hi, __shfl_sync(FULL, oend, 31));
-        const T g = pull_min<T>(a, beg, o, x, stop, red);
+        const T gmin = pull_min<MULTI, T>(a, beg, o, vw, x, stop, red);
         // finish the lifts of this window's entries
         bool changed = false;
         int pwork = 0;
         if (valid && o < stop && oend > x) {
-            if (o >= lo) atomicAnd(bits + (v >> 5), ~(1u << (v & 31)));  // consumed
+            if (o >= lo) atomicAnd(bits + (g >> 5), ~(1u << (g & 31)));  // consumed
             const int seen = min(oend, stop) - max(o, x);
-            T res = g;
+            T res = gmin;
             bool done = true;
             if (seen != oend - o) {  // lift split across warps: merge partial minima
-                atomicMin(a.acc + v, g);
+                atomicMin(a.acc + g, gmin);
                 __threadfence();
-                const int before = atomicAdd(a.acc_done + v, seen);
+                const int before = atomicAdd(a.acc_done + g, seen);
                 done = before + seen == oend - o;
                 if (done) {
                     __threadfence();
-                    res = xchg(a.acc + v, Cred<T>::TOP);
-                    atomicExch(a.acc_done + v, 0);
+                    res = xchg(a.acc + g, Cred<T>::TOP);
+                    atomicExch(a.acc_done + g, 0);
                 }
             }
-            if (done && res > ld_cg(a.f + v) && res > atomicMax(a.f + v, res)) {
+            if (done && res > ld_cg(a.f + g) && res > atomicMax(a.f + g, res)) {
                 pwork = __ldg(A.rrow_ptr + v + 1) - __ldg(A.rrow_ptr + v);
                 if (pwork > 0) {
-                    const unsigned bit = 1u << (v & 31);
-                    changed = !(ld_cg(bits_q + (v >> 5)) & bit) && !(atomicOr(bits_q + (v >> 5), bit) & bit);
+                    const unsigned bit = 1u << (g & 31);
+                    changed = !(ld_cg(bits_q + (g >> 5)) & bit) && !(atomicOr(bits_q + (g >> 5), bit) & bit);
                 }
             }
         }
-        warp_append(changed, (unsigned)v, pwork, &a.ctrl->push_ctr[r % 3], a.push_items[r & 1],
+        warp_append(changed, (unsigned)g, pwork, &a.ctrl->push_ctr[r % 3], a.push_items[r & 1],
                     a.push_offs[r & 1]);
         x = stop;
         i += 32;
@@ -492,7 +594,7 @@ __device__ void pull_phase(const Args<T> &a, int r, T *red) {
 // ---------------------------------------------------------------------------
 // Push phase: send the rises of the push list of round r to predecessors,
 // then work through the warp's local worklist.
-template <typename T>
+template <bool MULTI, typename T>
 __device__ void push_phase(const Args<T> &a, int r, T *red, Local<T> &L) {
     const DevArena &A = a.A;
     const int lane = lane_id();
@@ -519,25 +621,28 @@ __device__ void push_phase(const Args<T> &a, int r, T *red, Local<T> &L) {
         const bool valid = ii < cnt;
         int o = total, oend = total, beg = 0;
         T val = T(0);
+        View vw = idle_view<MULTI>(a);
         if (valid) {
-            const int v = ld_cg(items + ii) & 0x7fffffff;
+            const int g = ld_cg(items + ii) & 0x7fffffff;
+            vw = view_of<MULTI>(a, g);
+            const int v = g - vw.delta;
             o = ld_cg(offs + ii);
             oend = ii + 1 < cnt ? ld_cg(offs + ii + 1) : total;
             beg = __ldg(A.rrow_ptr + v);
-            if (o >= lo && o < hi) atomicAnd(bits_cur + (v >> 5), ~(1u << (v & 31)));  // consumed
-            val = ld_cg(a.f + v);
+            if (o >= lo && o < hi) atomicAnd(bits_cur + (g >> 5), ~(1u << (g & 31)));  // consumed
+            val = ld_cg(a.f + g);
         }
         const int stop = min(hi, __shfl_sync(FULL, oend, 31));
-        push_edges<T>(a, r, beg, o, val, x, stop, L);
+        push_edges<MULTI, T>(a, r, beg, o, val, vw, x, stop, L);
         x = stop;
         i += 32;
     }
-    drain_local<T>(a, r, red, L);
+    drain_local<MULTI, T>(a, r, red, L);
 }
 
 // ---------------------------------------------------------------------------
 // Persistent fixpoint kernel (Algorithm 3's while-loop on the device).
-template <typename T>
+template <bool MULTI, typename T>
 __global__ void __launch_bounds__(THREADS) k_fixpoint(Args<T> a) {
     __shared__ T red_all[WARPS][32];
     __shared__ int stack_all[WARPS][LOCAL_CAP];
@@ -561,11 +666,11 @@ __global__ void __launch_bounds__(THREADS) k_fixpoint(Args<T> a) {
         }
         const unsigned long long pc = ld_cg(&c->pull_ctr[r % 3]);
         if ((pc & 0xffffffffu) != 0) {
-            pull_phase<T>(a, r, red);
+            pull_phase<MULTI, T>(a, r, red);
             if (!grid_barrier(c, gridDim.x, gen, BARRIER_LIMIT_NS)) break;
         }
         const unsigned long long qc = ld_cg(&c->push_ctr[r % 3]);
-        push_phase<T>(a, r, red, L);
+        push_phase<MULTI, T>(a, r, red, L);
         if (!grid_barrier(c, gridDim.x, gen, BARRIER_LIMIT_NS)) break;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             c->rounds += 1;
@@ -631,10 +736,11 @@ eg_status free_state(StateBuffers &sb) {
 
 static size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
-static eg_status ensure_state(eg_arena *ar, int bits) {
-    StateBuffers &sb = bits == 32 ? ar->st32 : ar->st64;
-    if (sb.bits == bits) return EG_OK;
-    const size_t n = (size_t)ar->n, cs = bits / 8, words = (n + 31) / 32;
+// Solve state for nf credits of the given width.
+eg_status alloc_state(StateBuffers &sb, long long nf, int bits) {
+    if (sb.bits == bits && sb.nf == nf) return EG_OK;
+    free_state(sb);
+    const size_t n = (size_t)nf, cs = bits / 8, words = (n + 31) / 32;
     size_t off = 0;
     size_t o_f = off; off = align_up(off + n * cs);
     size_t o_list[8];
@@ -649,6 +755,7 @@ static eg_status ensure_state(eg_arena *ar, int bits) {
     sb.block = blk;
     sb.bytes = off;
     sb.bits = bits;
+    sb.nf = nf;
     sb.dirty = true;
     sb.d.f = blk + o_f;
     for (int k = 0; k < 2; ++k) {
@@ -666,24 +773,38 @@ static eg_status ensure_state(eg_arena *ar, int bits) {
     return EG_OK;
 }
 
-template <typename T>
-static eg_status launch_solve(eg_arena *ar, StateBuffers &sb, const WeightView &W, cudaStream_t s,
-                              long long max_rounds) {
-    const int n = ar->n;
-    const int sms = num_sms(ar->device);
+static eg_status ensure_state(eg_arena *ar, int bits) {
+    return alloc_state(bits == 32 ? ar->st32 : ar->st64, ar->n, bits);
+}
+
+// Launch parameters shared by single and batched solves.
+struct Launch {
+    int local_windows, local_maxdeg, warm_start;
+    long long seed_max_pairs, max_rounds;
+};
+
+// Enqueues (warm start,) initialisation and the persistent fixpoint on
+// stream s; ev_k (optional) is recorded right before the fixpoint kernel.
+template <bool MULTI, typename T>
+static eg_status enqueue_solve(const DevArena &A, const WeightView &W, const InstTable &I, long long nf,
+                               StateBuffers &sb, const Launch &L, int device, cudaStream_t s, cudaEvent_t ev_k) {
+    const int sms = num_sms(device);
     if (sb.dirty) {
-        k_fill<T><<<sms * 4, 256, 0, s>>>((T *)sb.d.acc, n, Cred<T>::TOP);
-        EG_CUDA_TRY(cudaMemsetAsync(sb.d.acc_done, 0, (size_t)n * 4, s));
+        k_fill<T><<<sms * 4, 256, 0, s>>>((T *)sb.d.acc, nf, Cred<T>::TOP);
+        EG_CUDA_TRY(cudaGetLastError());
+        EG_CUDA_TRY(cudaMemsetAsync(sb.d.acc_done, 0, (size_t)nf * 4, s));
         for (int k = 0; k < 2; ++k) {
-            EG_CUDA_TRY(cudaMemsetAsync(sb.d.bits_pull[k], 0, ((size_t)n + 31) / 32 * 4, s));
-            EG_CUDA_TRY(cudaMemsetAsync(sb.d.bits_push[k], 0, ((size_t)n + 31) / 32 * 4, s));
+            EG_CUDA_TRY(cudaMemsetAsync(sb.d.bits_pull[k], 0, ((size_t)nf + 31) / 32 * 4, s));
+            EG_CUDA_TRY(cudaMemsetAsync(sb.d.bits_push[k], 0, ((size_t)nf + 31) / 32 * 4, s));
         }
         sb.dirty = false;
     }
     EG_CUDA_TRY(cudaMemsetAsync(sb.d.ctrl, 0, sizeof(Ctrl), s));
     Args<T> a;
-    a.A = ar->d;
+    a.A = A;
     a.W = W;
+    a.I = I;
+    a.nf = (int)nf;
     a.f = (T *)sb.d.f;
     for (int k = 0; k < 2; ++k) {
         a.pull_items[k] = sb.d.pull_items[k];
@@ -696,33 +817,42 @@ static eg_status launch_solve(eg_arena *ar, StateBuffers &sb, const WeightView &
     a.acc = (T *)sb.d.acc;
     a.acc_done = sb.d.acc_done;
     a.ctrl = sb.d.ctrl;
-    a.max_rounds = max_rounds;
-    a.local_windows = ar->local_windows;
-    a.local_maxdeg = ar->local_maxdeg;
-
-    EG_CUDA_TRY(cudaEventRecord(ar->ev0, s));
+    a.max_rounds = L.max_rounds;
+    a.local_windows = L.local_windows;
+    a.local_maxdeg = L.local_maxdeg;
     a.seed_bits = nullptr;
-    if (ar->warm_start) {
-        EG_CUDA_TRY(cudaMemsetAsync(sb.d.seed_bits, 0, ((size_t)n + 31) / 32 * 4, s));
-        const int sblocks = (int)std::min<long long>(((long long)n + 7) / 8, (long long)sms * 32);
-        k_seed<<<sblocks, 256, 0, s>>>(ar->d, W, ar->seed_max_pairs, sb.d.seed_bits, &sb.d.ctrl->seeded);
+    if (L.warm_start) {
+        EG_CUDA_TRY(cudaMemsetAsync(sb.d.seed_bits, 0, ((size_t)nf + 31) / 32 * 4, s));
+        const int sblocks = (int)std::min<long long>((nf + 7) / 8, (long long)sms * 32);
+        k_seed<MULTI, T><<<sblocks, 256, 0, s>>>(a, L.seed_max_pairs, sb.d.seed_bits, &sb.d.ctrl->seeded);
         EG_CUDA_TRY(cudaGetLastError());
         a.seed_bits = sb.d.seed_bits;
     }
-    const int init_blocks = (int)std::min<long long>((n + THREADS - 1) / THREADS, (long long)sms * 16);
-    k_init<T><<<init_blocks, THREADS, 0, s>>>(a);
+    const int init_blocks = (int)std::min<long long>((nf + THREADS - 1) / THREADS, (long long)sms * 16);
+    k_init<MULTI, T><<<init_blocks, THREADS, 0, s>>>(a);
     EG_CUDA_TRY(cudaGetLastError());
 
     int per_sm = 0;
-    EG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fixpoint<T>, THREADS, 0));
+    EG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fixpoint<MULTI, T>, THREADS, 0));
     if (per_sm < 1) {
         set_error("fixpoint kernel cannot be resident");
         return EG_ERR_CUDA;
     }
     dim3 grid(sms * per_sm), block(THREADS);
     void *args[] = {&a};
-    EG_CUDA_TRY(cudaEventRecord(ar->evk, s));
-    EG_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_fixpoint<T>, grid, block, args, 0, s));
+    if (ev_k) EG_CUDA_TRY(cudaEventRecord(ev_k, s));
+    EG_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_fixpoint<MULTI, T>, grid, block, args, 0, s));
+    return EG_OK;
+}
+
+template <typename T>
+static eg_status launch_solve(eg_arena *ar, StateBuffers &sb, const WeightView &W, cudaStream_t s,
+                              long long max_rounds) {
+    Launch L{ar->local_windows, ar->local_maxdeg, ar->warm_start, ar->seed_max_pairs, max_rounds};
+    EG_CUDA_TRY(cudaEventRecord(ar->ev0, s));
+    InstTable none{1, nullptr, nullptr, nullptr, nullptr, nullptr};
+    eg_status rc = enqueue_solve<false, T>(ar->d, W, none, ar->n, sb, L, ar->device, s, ar->evk);
+    if (rc != EG_OK) return rc;
     EG_CUDA_TRY(cudaEventRecord(ar->ev1, s));
     return EG_OK;
 }
@@ -811,3 +941,331 @@ eg_status solve(eg_arena *ar, int credit_bits, long long scale, long long shift,
 }
 
 }  // namespace eg
+
+namespace eg {
+
+// ---------------------------------------------------------------------------
+// Batched solves (eg_plan).  Instances are laid out back to back in one
+// credit array; a table maps each credit index to its instance's arena view.
+// The solve (warm start, init, fixpoint, counter read-back) is captured once
+// into a CUDA graph and replayed by every run.
+
+struct eg_plan_impl {
+    eg_arena *ar = nullptr;
+    int count = 0;
+    long long nf = 0;
+    int bits = 32;       // computed in
+    int out_bits = 64;   // written out
+    std::vector<int> fbase, delta, n_of, bits_alone;
+    std::vector<long long> scale, shift, C;
+    void *table = nullptr;  // device instance table
+    InstTable I{};
+    StateBuffers sb;
+    cudaStream_t own = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, evk = nullptr;
+    void *host_ctrl = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    long long graph_rounds = -1;
+    int graph_opts[3] = {-1, -1, -1};
+    long long graph_pairs = -1;
+    bool graph_failed = false;
+};
+
+static eg_status plan_destroy(eg_plan_impl *p) {
+    if (!p) return EG_OK;
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    free_state(p->sb);
+    if (p->table) cudaFree(p->table);
+    if (p->own) cudaStreamDestroy(p->own);
+    if (p->ev0) cudaEventDestroy(p->ev0);
+    if (p->ev1) cudaEventDestroy(p->ev1);
+    if (p->evk) cudaEventDestroy(p->evk);
+    if (p->host_ctrl) cudaFreeHost(p->host_ctrl);
+    delete p;
+    return EG_OK;
+}
+
+eg_status plan_create(eg_arena *ar, int count, const int32_t *part, const int64_t *w_scale, const int64_t *w_shift,
+                      int credit_bits, eg_plan_impl **out) {
+    *out = nullptr;
+    if (count < 1) {
+        set_error("count must be >= 1");
+        return EG_ERR_INVALID;
+    }
+    if (credit_bits != 0 && credit_bits != 32 && credit_bits != 64) {
+        set_error("credit_bits must be 0, 32 or 64");
+        return EG_ERR_INVALID;
+    }
+    std::vector<long long> pp = ar->part_ptr;
+    if (pp.empty()) pp = {0, (long long)ar->n};
+    const int parts = (int)pp.size() - 1;
+    eg_plan_impl *p = new (std::nothrow) eg_plan_impl();
+    if (!p) {
+        set_error("host allocation failed");
+        return EG_ERR_OOM;
+    }
+    p->ar = ar;
+    p->count = count;
+    p->fbase.resize(count + 1);
+    p->delta.resize(count);
+    p->n_of.resize(count);
+    p->scale.resize(count);
+    p->shift.resize(count);
+    long long nf = 0;
+    for (int i = 0; i < count; ++i) {
+        const int k = part ? part[i] : i;
+        if (k < 0 || k >= parts) {
+            set_error("instance %d names game %d of %d", i, k, parts);
+            plan_destroy(p);
+            return EG_ERR_INVALID;
+        }
+        const long long sc = w_scale ? w_scale[i] : 1, sh = w_shift ? w_shift[i] : 0;
+        if ((sc < 0 ? -sc : sc) > (1LL << 30) || (sh < 0 ? -sh : sh) > (1LL << 61)) {
+            set_error("weight map of instance %d out of range", i);
+            plan_destroy(p);
+            return EG_ERR_INVALID;
+        }
+        p->fbase[i] = (int)nf;
+        p->delta[i] = (int)(nf - pp[k]);
+        p->n_of[i] = (int)(pp[k + 1] - pp[k]);
+        p->scale[i] = sc;
+        p->shift[i] = sh;
+        nf += pp[k + 1] - pp[k];
+        if (nf >= (1LL << 31) - 1) {
+            set_error("instances hold more than 2^31 - 1 credits");
+            plan_destroy(p);
+            return EG_ERR_INVALID;
+        }
+    }
+    p->fbase[count] = (int)nf;
+    p->nf = nf;
+    cudaStream_t s = nullptr;
+#define PTRY(expr)                                                          \
+    do {                                                                    \
+        cudaError_t _e = (expr);                                            \
+        if (_e != cudaSuccess) {                                            \
+            set_error("%s failed: %s", #expr, cudaGetErrorString(_e));      \
+            plan_destroy(p);                                                \
+            return _e == cudaErrorMemoryAllocation ? EG_ERR_OOM : EG_ERR_CUDA; \
+        }                                                                   \
+    } while (0)
+    PTRY(cudaStreamCreateWithFlags(&p->own, cudaStreamNonBlocking));
+    s = p->own;
+    PTRY(cudaEventCreate(&p->ev0));
+    PTRY(cudaEventCreate(&p->ev1));
+    PTRY(cudaEventCreate(&p->evk));
+    PTRY(cudaMallocHost(&p->host_ctrl, sizeof(Ctrl)));
+    // device table: fbase (count+1 ints), delta (count ints), scale, shift, C (count long longs), and
+    // per-instance bound accumulators
+    const size_t ints = (size_t)2 * count + 1;
+    const size_t off_ll = ((ints * 4 + 15) / 16) * 16;
+    const size_t bytes = off_ll + (size_t)5 * count * 8;
+    char *tb = nullptr;
+    PTRY(cudaMalloc((void **)&tb, bytes));
+    p->table = tb;
+    int *d_fbase = (int *)tb, *d_delta = d_fbase + count + 1;
+    long long *d_scale = (long long *)(tb + off_ll), *d_shift = d_scale + count, *d_C = d_shift + count;
+    unsigned long long *d_accC = (unsigned long long *)(d_C + count), *d_accW = d_accC + count;
+    PTRY(cudaMemcpyAsync(d_fbase, p->fbase.data(), (count + 1) * 4, cudaMemcpyHostToDevice, s));
+    PTRY(cudaMemcpyAsync(d_delta, p->delta.data(), count * 4, cudaMemcpyHostToDevice, s));
+    PTRY(cudaMemcpyAsync(d_scale, p->scale.data(), count * 8, cudaMemcpyHostToDevice, s));
+    PTRY(cudaMemcpyAsync(d_shift, p->shift.data(), count * 8, cudaMemcpyHostToDevice, s));
+    PTRY(cudaMemsetAsync(d_accC, 0, (size_t)2 * count * 8, s));
+    p->I = InstTable{count, d_fbase, d_delta, d_scale, d_shift, d_C};
+    const int sms = num_sms(ar->device);
+    k_bound_inst<<<(int)std::min<long long>((nf + 255) / 256, (long long)sms * 32), 256, 0, s>>>(
+        ar->d, p->I, (int)nf, d_accC, d_accW);
+    PTRY(cudaGetLastError());
+    std::vector<unsigned long long> hc(2 * (size_t)count);
+    PTRY(cudaMemcpyAsync(hc.data(), d_accC, (size_t)2 * count * 8, cudaMemcpyDeviceToHost, s));
+    PTRY(cudaStreamSynchronize(s));
+    p->C.resize(count);
+    p->bits_alone.resize(count);
+    bool all32 = true;
+    for (int i = 0; i < count; ++i) {
+        p->C[i] = (long long)hc[i];
+        const bool fits = (long long)hc[i] + (long long)hc[count + i] <= 0x7fffffffLL - 1;
+        p->bits_alone[i] = fits ? 32 : 64;
+        all32 = all32 && fits;
+    }
+    if (credit_bits == 32 && !all32) {
+        set_error("int32 credits cannot hold every instance");
+        plan_destroy(p);
+        return EG_ERR_OVERFLOW;
+    }
+    p->bits = (credit_bits == 64 || !all32) ? 64 : 32;
+    p->out_bits = credit_bits == 32 ? 32 : 64;
+    PTRY(cudaMemcpyAsync(d_C, p->C.data(), count * 8, cudaMemcpyHostToDevice, s));
+    eg_status rc = alloc_state(p->sb, nf, p->bits);
+    if (rc != EG_OK) {
+        plan_destroy(p);
+        return rc;
+    }
+    PTRY(cudaStreamSynchronize(s));
+#undef PTRY
+    *out = p;
+    return EG_OK;
+}
+
+// Enqueues one batched solve on s (also used under stream capture).
+static eg_status plan_enqueue(eg_plan_impl *p, const Launch &L, cudaStream_t s, cudaEvent_t evk) {
+    WeightView W{1, 0, 0};
+    eg_status rc = p->bits == 32
+                       ? enqueue_solve<true, int>(p->ar->d, W, p->I, p->nf, p->sb, L, p->ar->device, s, evk)
+                       : enqueue_solve<true, long long>(p->ar->d, W, p->I, p->nf, p->sb, L, p->ar->device, s, evk);
+    if (rc != EG_OK) return rc;
+    EG_CUDA_TRY(cudaMemcpyAsync(p->host_ctrl, p->sb.d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    return EG_OK;
+}
+
+eg_status plan_run(eg_plan_impl *p, void *out, eg_stats *st, cudaStream_t user, long long max_rounds) {
+    eg_arena *ar = p->ar;
+    const Launch L{ar->local_windows, ar->local_maxdeg, ar->warm_start, ar->seed_max_pairs, max_rounds};
+    cudaStream_t s = user ? user : p->own;
+    // scratch left dirty by an aborted run is reset outside the graph
+    if (p->sb.dirty) {
+        const int sms = num_sms(ar->device);
+        if (p->bits == 32) k_fill<int><<<sms * 4, 256, 0, s>>>((int *)p->sb.d.acc, p->nf, Cred<int>::TOP);
+        else k_fill<long long><<<sms * 4, 256, 0, s>>>((long long *)p->sb.d.acc, p->nf, Cred<long long>::TOP);
+        EG_CUDA_TRY(cudaMemsetAsync(p->sb.d.acc_done, 0, (size_t)p->nf * 4, s));
+        for (int k = 0; k < 2; ++k) {
+            EG_CUDA_TRY(cudaMemsetAsync(p->sb.d.bits_pull[k], 0, ((size_t)p->nf + 31) / 32 * 4, s));
+            EG_CUDA_TRY(cudaMemsetAsync(p->sb.d.bits_push[k], 0, ((size_t)p->nf + 31) / 32 * 4, s));
+        }
+        p->sb.dirty = false;
+    }
+    const bool same = p->graph && p->graph_rounds == max_rounds && p->graph_opts[0] == L.local_windows &&
+                      p->graph_opts[1] == L.local_maxdeg && p->graph_opts[2] == L.warm_start &&
+                      p->graph_pairs == L.seed_max_pairs;
+    if (!ar->use_graph && p->graph) {
+        cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+    }
+    if (ar->use_graph && !same && !p->graph_failed) {
+        if (p->graph) {
+            cudaGraphExecDestroy(p->graph);
+            p->graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        bool ok = cudaStreamBeginCapture(p->own, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            eg_status rc = plan_enqueue(p, L, p->own, nullptr);
+            ok = cudaStreamEndCapture(p->own, &g) == cudaSuccess && rc == EG_OK && g;
+        }
+        if (ok) ok = cudaGraphInstantiate(&p->graph, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        if (ok) {
+            p->graph_rounds = max_rounds;
+            p->graph_opts[0] = L.local_windows;
+            p->graph_opts[1] = L.local_maxdeg;
+            p->graph_opts[2] = L.warm_start;
+            p->graph_pairs = L.seed_max_pairs;
+        } else {
+            p->graph = nullptr;
+            p->graph_failed = true;  // capture unsupported here: launch directly from now on
+        }
+    }
+    EG_CUDA_TRY(cudaEventRecord(p->ev0, s));
+    if (p->graph) {
+        EG_CUDA_TRY(cudaGraphLaunch(p->graph, s));
+    } else {
+        eg_status rc = plan_enqueue(p, L, s, p->evk);
+        if (rc != EG_OK) return rc;
+    }
+    EG_CUDA_TRY(cudaEventRecord(p->ev1, s));
+    // credits out
+    cudaPointerAttributes attr{};
+    const bool dev_out = cudaPointerGetAttributes(&attr, out) == cudaSuccess &&
+                         (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    void *src = p->sb.d.f, *tmp = nullptr;
+    if (p->out_bits != p->bits) {
+        EG_CUDA_TRY(cudaMallocAsync(&tmp, (size_t)p->nf * 8, s));
+        k_widen<<<(int)std::min<long long>((p->nf + 255) / 256, 4096), 256, 0, s>>>((const int *)p->sb.d.f,
+                                                                                    (long long *)tmp, (int)p->nf);
+        EG_CUDA_TRY(cudaGetLastError());
+        src = tmp;
+    }
+    EG_CUDA_TRY(cudaMemcpyAsync(out, src, (size_t)p->nf * (p->out_bits / 8),
+                                dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (tmp) EG_CUDA_TRY(cudaFreeAsync(tmp, s));
+    EG_CUDA_TRY(cudaStreamSynchronize(s));
+    const Ctrl *hc = (const Ctrl *)p->host_ctrl;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p->ev0, p->ev1);
+    eg_status result = EG_OK;
+    if (hc->status == DEV_TIMEOUT) {
+        set_error("a device-side wait exceeded its limit");
+        result = EG_ERR_TIMEOUT;
+        p->sb.dirty = true;
+    } else if (hc->status == DEV_BUDGET) {
+        set_error("round budget of %lld exhausted", max_rounds);
+        result = EG_ERR_BUDGET;
+        p->sb.dirty = true;
+    }
+    if (st) {
+        long long cmax = 0;
+        for (long long c : p->C) cmax = std::max(cmax, c);
+        st->C = cmax;
+        st->seeded = (int64_t)hc->seeded;
+        st->credit_bits = p->bits;
+        st->status = result;
+        st->rounds = (int64_t)hc->rounds;
+        st->lifts = (int64_t)hc->lifts;
+        st->pushes = (int64_t)hc->pushes;
+        st->relaxations = (int64_t)hc->relax;
+        st->enqueues = (int64_t)hc->enqueues;
+        st->ms = ms;
+        st->fixpoint_ms = p->graph ? -1.0 : ms;
+    }
+    return result;
+}
+
+}  // namespace eg
+
+struct eg_plan : eg::eg_plan_impl {};
+
+extern "C" {
+
+eg_status eg_plan_create(eg_arena *arena, int32_t count, const int32_t *part, const int64_t *w_scale,
+                         const int64_t *w_shift, int32_t credit_bits, eg_plan **out) {
+    eg::clear_error();
+    if (!arena || !out) {
+        eg::set_error("arena and out are required");
+        return EG_ERR_INVALID;
+    }
+    eg::eg_plan_impl *p = nullptr;
+    eg_status rc = eg::plan_create(arena, count, part, w_scale, w_shift, credit_bits, &p);
+    *out = (eg_plan *)p;
+    return rc;
+}
+
+eg_status eg_plan_instance(eg_plan *plan, int32_t i, int64_t *offset, int64_t *n, int64_t *C, int32_t *bits) {
+    eg::clear_error();
+    if (!plan || i < 0 || i >= plan->count) {
+        eg::set_error("no such instance");
+        return EG_ERR_INVALID;
+    }
+    if (offset) *offset = plan->fbase[i];
+    if (n) *n = plan->n_of[i];
+    if (C) *C = plan->C[i];
+    if (bits) *bits = plan->bits_alone[i];
+    return EG_OK;
+}
+
+eg_status eg_plan_run(eg_plan *plan, void *credits_out, eg_stats *st, void *cuda_stream, int64_t max_rounds) {
+    eg::clear_error();
+    if (!plan || !credits_out) {
+        eg::set_error("plan and credits_out are required");
+        return EG_ERR_INVALID;
+    }
+    return eg::plan_run(plan, credits_out, st, (cudaStream_t)cuda_stream, max_rounds);
+}
+
+eg_status eg_plan_destroy(eg_plan *plan) {
+    eg::clear_error();
+    return eg::plan_destroy(plan);
+}
+
+}  // extern "C"

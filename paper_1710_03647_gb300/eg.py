@@ -61,6 +61,12 @@ SIGNATURES = {
     "eg_bound": (_I32, [_P, _I64, _I64, ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
     "eg_solve_credit": (_I32, [_P, _I32, _I64, _I64, _P, ctypes.POINTER(eg_stats), _P, _I64]),
     "eg_set_option": (_I32, [_P, _I32, _I64]),
+    "eg_set_parts": (_I32, [_P, _I32, _P]),
+    "eg_plan_create": (_I32, [_P, _I32, _P, _P, _P, _I32, ctypes.POINTER(_P)]),
+    "eg_plan_instance": (_I32, [_P, _I32, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64),
+                                ctypes.POINTER(_I32)]),
+    "eg_plan_run": (_I32, [_P, _P, ctypes.POINTER(eg_stats), _P, _I64]),
+    "eg_plan_destroy": (_I32, [_P]),
     "eg_last_error": (ctypes.c_char_p, []),
     "eg_version": (ctypes.c_char_p, []),
 }
@@ -136,6 +142,7 @@ EG_OPT_LOCAL_WINDOWS = 1
 EG_OPT_LOCAL_MAXDEG = 2
 EG_OPT_WARM_START = 3
 EG_OPT_SEED_MAX_PAIRS = 4
+EG_OPT_GRAPH = 5
 
 
 def eg_set_option(arena, option: int, value: int) -> None:
@@ -188,6 +195,96 @@ class Arena:
     def close(self):
         if self.handle:
             eg_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def eg_set_parts(arena, part_ptr) -> None:
+    pp = np.ascontiguousarray(part_ptr, dtype=np.int64)
+    _check(load().eg_set_parts(arena, pp.shape[0] - 1, pp.ctypes.data))
+
+
+def pack_games(games):
+    """Disjoint union of arenas (objects with n, row_ptr, col, w, owner_bits):
+    returns (n, row_ptr, col, w, owner_bits, part_ptr) with game k's vertex v
+    at part_ptr[k] + v."""
+    ns = [int(g.n) for g in games]
+    part_ptr = np.zeros(len(games) + 1, dtype=np.int64)
+    np.cumsum(ns, out=part_ptr[1:])
+    ms = [int(g.row_ptr[-1]) for g in games]
+    eoff = np.concatenate([[0], np.cumsum(ms)]).astype(np.int64)
+    n = int(part_ptr[-1])
+    row_ptr = np.empty(n + 1, dtype=np.int64)
+    col = np.empty(int(eoff[-1]), dtype=np.int32)
+    w = np.empty(int(eoff[-1]), dtype=np.int32)
+    own = np.zeros(n, dtype=bool)
+    for k, g in enumerate(games):
+        a, b = int(part_ptr[k]), int(part_ptr[k + 1])
+        row_ptr[a:b] = np.asarray(g.row_ptr[:-1], dtype=np.int64) + eoff[k]
+        col[eoff[k]:eoff[k + 1]] = np.asarray(g.col, dtype=np.int64) + a
+        w[eoff[k]:eoff[k + 1]] = g.w
+        idx = np.arange(g.n)
+        own[a:b] = (np.asarray(g.owner_bits, dtype=np.uint32)[idx >> 5] >> (idx & 31).astype(np.uint32)) & 1
+    row_ptr[n] = eoff[-1]
+    words = (n + 31) // 32
+    padded = np.zeros(words * 32, dtype=np.uint64)
+    padded[:n] = own
+    owner_bits = (padded.reshape(words, 32) << np.arange(32, dtype=np.uint64)).sum(axis=1).astype(np.uint32)
+    return n, row_ptr, col, w, owner_bits, part_ptr
+
+
+class Plan:
+    """A batched solve: count instances (game part[i] under w' = scale*w - shift)."""
+
+    def __init__(self, arena_handle, count, part=None, w_scale=None, w_shift=None, credit_bits=0):
+        self._keep = []
+
+        def arr(x, dt):
+            if x is None:
+                return None
+            a = np.ascontiguousarray(x, dtype=dt)
+            self._keep.append(a)
+            return a.ctypes.data
+
+        out = _P()
+        _check(load().eg_plan_create(arena_handle, count, arr(part, np.int32), arr(w_scale, np.int64),
+                                     arr(w_shift, np.int64), credit_bits, ctypes.byref(out)))
+        self.handle = out.value
+        self.count = count
+        self.credit_bits = credit_bits
+        self.total = sum(self.instance(i)[1] for i in range(count))
+
+    def instance(self, i):
+        """(offset, n, C, bits the instance alone needs)"""
+        off, n, C, b = _I64(), _I64(), _I64(), _I32()
+        _check(load().eg_plan_instance(self.handle, i, ctypes.byref(off), ctypes.byref(n), ctypes.byref(C),
+                                       ctypes.byref(b)))
+        return off.value, n.value, C.value, b.value
+
+    def run(self, out=None, stream=None, max_rounds=0, raise_on_error=True):
+        if out is None:
+            out = np.empty(self.total, dtype=np.int32 if self.credit_bits == 32 else np.int64)
+        st = eg_stats()
+        ptr = out.ctypes.data if isinstance(out, np.ndarray) else _addr(out, None)
+        rc = load().eg_plan_run(self.handle, ptr, ctypes.byref(st), stream, max_rounds)
+        if raise_on_error:
+            _check(rc)
+        return out, st
+
+    def close(self):
+        if self.handle:
+            _check(load().eg_plan_destroy(self.handle))
             self.handle = None
 
     def __enter__(self):
