@@ -198,6 +198,33 @@ eg_status eg_plan_instance(eg_plan *plan, int32_t i, int64_t *offset, int64_t *n
 eg_status eg_plan_run(eg_plan *plan, void *credits_out, eg_stats *st, void *cuda_stream, int64_t max_rounds);
 eg_status eg_plan_destroy(eg_plan *plan);
 
+/*
+ * eg_solve_credit_noalloc -- eg_solve_credit for callers that cannot
+ * allocate device memory at solve time: a program whose framework has
+ * already handed the GPU's memory to its own caching allocator, or a
+ * latency-bound loop where cudaMalloc / cudaFree would synchronise the
+ * device and stall other streams.  The paper has no counterpart; it is a
+ * deployment variant of the same solve with the same results.
+ *
+ * It allocates nothing: its working memory is one fixed device array inside
+ * the library (held by every GPU that loads the library until the process
+ * exits), and credits_out -- device memory, n elements of credit_bits (32 or
+ * 64 only) -- serves as the credit array while the solve runs.  The arena
+ * must have at most EG_NOALLOC_MAX_VERTICES vertices (EG_ERR_INVALID with a
+ * message otherwise) and must live on the current device.
+ *
+ * The first call on a device looks the working array up on that device; make
+ * that first call before any stream capture.  All calls share the one array
+ * and each call clears what it needs before use, so calls whose work
+ * overlaps on the GPU (other threads, or other streams without ordering
+ * between them) race and give undefined results: order them.  Synchronous,
+ * like eg_solve_credit; on EG_ERR_BUDGET / EG_ERR_TIMEOUT credits_out holds
+ * values below the least fixpoint.
+ */
+#define EG_NOALLOC_MAX_VERTICES (1 << 18)
+eg_status eg_solve_credit_noalloc(eg_arena *arena, int32_t credit_bits, int64_t w_scale, int64_t w_shift,
+                                  void *credits_out, eg_stats *st, void *cuda_stream, int64_t max_rounds);
+
 /* eg_last_error -- message of the calling thread's last failure ("" if none). */
 const char *eg_last_error(void);
 

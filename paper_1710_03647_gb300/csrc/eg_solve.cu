@@ -36,6 +36,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "eg_device.cuh"
 #include "eg_internal.h"
@@ -1269,3 +1270,179 @@ eg_status eg_plan_destroy(eg_plan *plan) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free single solve.
+//
+// Some callers cannot allocate device memory when they solve: a host program
+// whose framework has already reserved the GPU's memory for its own caching
+// allocator, or a latency-bound loop where a cudaMalloc / cudaFree would
+// synchronise the device and stall every other stream.  For them the solver
+// keeps its working memory (lists, dedupe bitmaps, partial minima, control
+// block) in one file-scope device array of fixed size, and it writes credits
+// straight into the caller's device output buffer, which doubles as the
+// credit array of the solve.  Every GPU that loads the library holds this
+// array until the process exits; every call reuses it.
+
+namespace eg {
+
+constexpr long long NOALLOC_MAX_N = EG_NOALLOC_MAX_VERTICES;
+constexpr size_t NOALLOC_WORDS = (size_t)(NOALLOC_MAX_N + 31) / 32;
+constexpr size_t noalloc_up(size_t x) { return (x + 255) & ~size_t(255); }
+// layout: 8 lists of n ints, 5 bitmaps, n partial minima (int64), n counts,
+// control block, two 64-bit bound accumulators
+constexpr size_t NA_LISTS = 0;
+constexpr size_t NA_BITS = NA_LISTS + 8 * noalloc_up((size_t)NOALLOC_MAX_N * 4);
+constexpr size_t NA_ACC = NA_BITS + 5 * noalloc_up(NOALLOC_WORDS * 4);
+constexpr size_t NA_DONE = NA_ACC + noalloc_up((size_t)NOALLOC_MAX_N * 8);
+constexpr size_t NA_CTRL = NA_DONE + noalloc_up((size_t)NOALLOC_MAX_N * 4);
+constexpr size_t NA_BOUND = NA_CTRL + noalloc_up(sizeof(Ctrl));
+constexpr size_t NA_BYTES = NA_BOUND + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
+
+// Device address of g_noalloc_scratch on each device, looked up once per
+// device (with that device current) on the first call made there.
+static void *g_noalloc_addr[64];
+static std::mutex g_noalloc_mu;
+
+static eg_status noalloc_scratch(int device, unsigned char **out) {
+    if (device < 0 || device >= 64) {
+        set_error("device ordinal %d out of range", device);
+        return EG_ERR_INVALID;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error("cudaGetSymbolAddress of the solver scratch failed: %s", cudaGetErrorString(e));
+            return EG_ERR_CUDA;
+        }
+        g_noalloc_addr[device] = p;
+    }
+    *out = (unsigned char *)g_noalloc_addr[device];
+    return EG_OK;
+}
+
+static eg_status solve_noalloc(eg_arena *ar, int credit_bits, long long scale, long long shift, void *out,
+                               eg_stats *st, cudaStream_t s, long long max_rounds) {
+    if (credit_bits != 32 && credit_bits != 64) {
+        set_error("credit_bits must be 32 or 64 (credits are computed in the output buffer)");
+        return EG_ERR_INVALID;
+    }
+    if (ar->n > NOALLOC_MAX_N) {
+        set_error("arena has %d vertices; the allocation-free solve holds at most %lld", ar->n, NOALLOC_MAX_N);
+        return EG_ERR_INVALID;
+    }
+    const long long sa = scale < 0 ? -scale : scale, sh = shift < 0 ? -shift : shift;
+    if (sa > (1LL << 30) || sh > (1LL << 61)) {
+        set_error("weight map out of range");
+        return EG_ERR_INVALID;
+    }
+    cudaPointerAttributes attr{};
+    if (cudaPointerGetAttributes(&attr, out) != cudaSuccess ||
+        (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)) {
+        cudaGetLastError();
+        set_error("credits_out must be device memory (it holds the credits during the solve)");
+        return EG_ERR_INVALID;
+    }
+    int device = 0;
+    EG_CUDA_TRY(cudaGetDevice(&device));
+    if (device != ar->device) {
+        set_error("the arena lives on device %d, the current device is %d", ar->device, device);
+        return EG_ERR_INVALID;
+    }
+    unsigned char *base = nullptr;
+    eg_status rc = noalloc_scratch(device, &base);
+    if (rc != EG_OK) return rc;
+
+    // bound C of the weight view, accumulated in the scratch
+    unsigned long long *dbound = (unsigned long long *)(base + NA_BOUND);
+    EG_CUDA_TRY(cudaMemsetAsync(dbound, 0, 16, s));
+    k_bound<<<num_sms(device) * 8, 256, 0, s>>>(ar->d, WeightView{scale, shift, 0}, dbound, dbound + 1);
+    EG_CUDA_TRY(cudaGetLastError());
+    EG_CUDA_TRY(cudaMemcpyAsync(ar->host_ctrl, dbound, 16, cudaMemcpyDeviceToHost, s));
+    EG_CUDA_TRY(cudaStreamSynchronize(s));
+    const long long C = (long long)((unsigned long long *)ar->host_ctrl)[0];
+    const long long wmax = (long long)((unsigned long long *)ar->host_ctrl)[1];
+    if (credit_bits == 32 && C + wmax > 0x7fffffffLL - 1) {
+        set_error("int32 credits cannot hold C + max|w'| = %lld", C + wmax);
+        return EG_ERR_OVERFLOW;
+    }
+
+    // solve state laid over the scratch; the output buffer is the credit array
+    const size_t n = (size_t)ar->n, words = (n + 31) / 32;
+    StateBuffers sb;
+    sb.bits = credit_bits;
+    sb.nf = ar->n;
+    sb.dirty = true;  // every call starts from cleared scratch
+    sb.d.f = out;
+    for (int k = 0; k < 2; ++k) {
+        sb.d.pull_items[k] = (int *)(base + NA_LISTS + (4 * k + 0) * noalloc_up(n * 4));
+        sb.d.pull_offs[k] = (int *)(base + NA_LISTS + (4 * k + 1) * noalloc_up(n * 4));
+        sb.d.push_items[k] = (int *)(base + NA_LISTS + (4 * k + 2) * noalloc_up(n * 4));
+        sb.d.push_offs[k] = (int *)(base + NA_LISTS + (4 * k + 3) * noalloc_up(n * 4));
+        sb.d.bits_pull[k] = (unsigned *)(base + NA_BITS + k * noalloc_up(words * 4));
+        sb.d.bits_push[k] = (unsigned *)(base + NA_BITS + (2 + k) * noalloc_up(words * 4));
+    }
+    sb.d.seed_bits = (unsigned *)(base + NA_BITS + 4 * noalloc_up(words * 4));
+    sb.d.acc = base + NA_ACC;
+    sb.d.acc_done = (int *)(base + NA_DONE);
+    sb.d.ctrl = (Ctrl *)(base + NA_CTRL);
+
+    const WeightView W{scale, shift, C};
+    const Launch L{ar->local_windows, ar->local_maxdeg, ar->warm_start, ar->seed_max_pairs, max_rounds};
+    InstTable none{1, nullptr, nullptr, nullptr, nullptr, nullptr};
+    EG_CUDA_TRY(cudaEventRecord(ar->ev0, s));
+    rc = credit_bits == 32 ? enqueue_solve<false, int>(ar->d, W, none, ar->n, sb, L, device, s, ar->evk)
+                           : enqueue_solve<false, long long>(ar->d, W, none, ar->n, sb, L, device, s, ar->evk);
+    if (rc != EG_OK) return rc;
+    EG_CUDA_TRY(cudaEventRecord(ar->ev1, s));
+    EG_CUDA_TRY(cudaMemcpyAsync(ar->host_ctrl, sb.d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    EG_CUDA_TRY(cudaStreamSynchronize(s));
+    const Ctrl *hc = (const Ctrl *)ar->host_ctrl;
+    float ms = 0.f, kms = 0.f;
+    cudaEventElapsedTime(&ms, ar->ev0, ar->ev1);
+    cudaEventElapsedTime(&kms, ar->evk, ar->ev1);
+    eg_status result = EG_OK;
+    if (hc->status == DEV_TIMEOUT) {
+        set_error("a device-side wait exceeded its limit");
+        result = EG_ERR_TIMEOUT;
+    } else if (hc->status == DEV_BUDGET) {
+        set_error("round budget of %lld exhausted", max_rounds);
+        result = EG_ERR_BUDGET;
+    }
+    if (st) {
+        st->C = C;
+        st->seeded = (int64_t)hc->seeded;
+        st->credit_bits = credit_bits;
+        st->status = result;
+        st->rounds = (int64_t)hc->rounds;
+        st->lifts = (int64_t)hc->lifts;
+        st->pushes = (int64_t)hc->pushes;
+        st->relaxations = (int64_t)hc->relax;
+        st->enqueues = (int64_t)hc->enqueues;
+        st->ms = ms;
+        st->fixpoint_ms = kms;
+    }
+    return result;
+}
+
+}  // namespace eg
+
+extern "C" eg_status eg_solve_credit_noalloc(eg_arena *arena, int32_t credit_bits, int64_t w_scale, int64_t w_shift,
+                                             void *credits_out, eg_stats *st, void *cuda_stream, int64_t max_rounds) {
+    eg::clear_error();
+    if (!arena || !credits_out) {
+        eg::set_error("arena and credits_out are required");
+        return EG_ERR_INVALID;
+    }
+    try {
+        return eg::solve_noalloc(arena, credit_bits, w_scale, w_shift, credits_out, st, (cudaStream_t)cuda_stream,
+                                 max_rounds);
+    } catch (...) {
+        eg::set_error("unexpected exception in eg_solve_credit_noalloc");
+        return EG_ERR_INVALID;
+    }
+}

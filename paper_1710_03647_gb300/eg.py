@@ -29,6 +29,7 @@ EG_ERR_BUSY = -8
 EG_TOP32 = np.iinfo(np.int32).max
 EG_TOP64 = np.iinfo(np.int64).max
 EG_INPUT_DEVICE = 1
+EG_NOALLOC_MAX_VERTICES = 1 << 18
 
 STATUS_NAMES = {0: "EG_OK", 1: "EG_PENDING", -1: "EG_ERR_INVALID", -2: "EG_ERR_NOT_TOTAL",
                 -3: "EG_ERR_OVERFLOW", -4: "EG_ERR_OOM", -5: "EG_ERR_CUDA", -6: "EG_ERR_TIMEOUT",
@@ -67,6 +68,7 @@ SIGNATURES = {
                                 ctypes.POINTER(_I32)]),
     "eg_plan_run": (_I32, [_P, _P, ctypes.POINTER(eg_stats), _P, _I64]),
     "eg_plan_destroy": (_I32, [_P]),
+    "eg_solve_credit_noalloc": (_I32, [_P, _I32, _I64, _I64, _P, ctypes.POINTER(eg_stats), _P, _I64]),
     "eg_last_error": (ctypes.c_char_p, []),
     "eg_version": (ctypes.c_char_p, []),
 }
@@ -143,6 +145,18 @@ EG_OPT_LOCAL_MAXDEG = 2
 EG_OPT_WARM_START = 3
 EG_OPT_SEED_MAX_PAIRS = 4
 EG_OPT_GRAPH = 5
+
+
+def eg_solve_credit_noalloc(arena, credit_bits, w_scale, w_shift, credits_out, stream=None, max_rounds=0,
+                            raise_on_error=True):
+    """Allocation-free solve; credits_out is a device buffer (address or
+    tensor) of n elements of credit_bits (32 or 64).  Returns (status, eg_stats)."""
+    st = eg_stats()
+    rc = load().eg_solve_credit_noalloc(arena, credit_bits, w_scale, w_shift, _addr(credits_out, None),
+                                        ctypes.byref(st), stream, max_rounds)
+    if raise_on_error:
+        _check(rc)
+    return rc, st
 
 
 def eg_set_option(arena, option: int, value: int) -> None:
