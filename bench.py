@@ -101,6 +101,17 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+def reduce_over_ranks(total_ms, relax, device, dist):
+    """Replicas: the job's time is the slowest rank's, its work the sum."""
+    import torch
+
+    t = torch.tensor([float(total_ms), float(relax)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -162,6 +173,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the context solve without warm start")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched threshold-query comparison")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -221,11 +233,7 @@ def main():
     relax = sum(x["relaxations"] for x in stats)
     launches = 3 * args.steps  # warm-start seed + init + persistent fixpoint per step
     if pg:
-        t = torch.tensor([total_ms, relax], dtype=torch.float64, device=dev)
-        tmax = t.clone()
-        pg.all_reduce(tmax, op=pg.ReduceOp.MAX)
-        pg.all_reduce(t, op=pg.ReduceOp.SUM)
-        total_ms_max, relax_all = float(tmax[0]), float(t[1])
+        total_ms_max, relax_all = reduce_over_ranks(total_ms, relax, dev, pg)
     else:
         total_ms_max, relax_all = total_ms, float(relax)
 
@@ -258,6 +266,47 @@ def main():
         e2e = {"value": e_relax / sum(e_times), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(host_out.nbytes + 128),
                "ms_per_step": 1e3 * sum(e_times) / len(e_times)}
+
+    # 256 mean-payoff threshold queries on the same arena (w' = 256 w - k W,
+    # k = -128..127, W = 100): one batched launch vs one solve per query
+    thresholds = None
+    if rank == 0 and not args.no_batch:
+        ks = list(range(-128, 128))
+        plan = eg.Plan(arena.handle, len(ks), part=[0] * len(ks), w_scale=[256] * len(ks),
+                       w_shift=[k * 100 for k in ks])
+        bout = torch.empty(plan.total, dtype=torch.int64, device=dev)
+        for _ in range(2):
+            plan.run(bout, stream=stream.cuda_stream)
+        bms, brelax = [], 0
+        for _ in range(3):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+            b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            b0.record(stream)
+            _, bst = plan.run(bout, stream=stream.cuda_stream)
+            b1.record(stream)
+            torch.cuda.synchronize()
+            bms.append(b0.elapsed_time(b1))
+            brelax = bst.relaxations
+        one = torch.empty(a.n, dtype=torch.int64, device=dev)
+        qms = []
+        for k in ks:
+            q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            q0.record(stream)
+            eg.eg_solve_credit(arena.handle, 64, 256, k * 100, one, stream=stream.cuda_stream)
+            q1.record(stream)
+            torch.cuda.synchronize()
+            qms.append(q0.elapsed_time(q1))
+        plan.close()
+        bmed = statistics.median(bms)
+        qms_sorted = sorted(qms)
+        thresholds = {"queries": len(ks), "batched_ms": bmed, "batched_games_per_s": len(ks) / (bmed * 1e-3),
+                      "batched_relaxations": brelax, "batched_p50_ms": bmed, "batched_p99_ms": max(bms),
+                      "per_query_total_ms": sum(qms), "per_query_games_per_s": len(ks) / (sum(qms) * 1e-3),
+                      "per_query_p50_ms": qms_sorted[len(qms) // 2],
+                      "per_query_p99_ms": qms_sorted[min(len(qms) - 1, int(0.99 * len(qms)))],
+                      "note": "batched: all queries in one persistent launch (CUDA graph); latency of every "
+                              "query = the batch time"}
 
     # the paper's start (f = 0 everywhere, no warm start), once, for context
     plain = None
@@ -300,6 +349,7 @@ def main():
         "cpu_baseline": cpu,
         "warm_start_seeded": st0["seeded"],
         "plain": plain,
+        "threshold_queries": thresholds,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk.summary(),

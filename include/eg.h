@@ -225,6 +225,34 @@ eg_status eg_plan_destroy(eg_plan *plan);
 eg_status eg_solve_credit_noalloc(eg_arena *arena, int32_t credit_bits, int64_t w_scale, int64_t w_shift,
                                   void *credits_out, eg_stats *st, void *cuda_stream, int64_t max_rounds);
 
+/*
+ * Serving.  A server owns a scheduler thread and a device memory budget.
+ * eg_submit queues a solve of `arena` under the map w' = w_scale * w -
+ * w_shift and returns a ticket at once.  The scheduler admits queued
+ * requests in arrival order while their memory (arena copy plus solve
+ * state, about 16 bytes per edge and 64 per vertex) fits the budget, up to
+ * max_batch of them, packs their arenas into one device arena and solves
+ * them in one batched launch (eg_plan).  Requests that arrive while a batch
+ * runs wait for the next batch, which starts as soon as the running one
+ * ends, so arrivals of different sizes share the device continuously.  The
+ * result of every request equals eg_solve_credit on its arena alone.
+ *
+ * eg_poll returns EG_PENDING until the request is done, then copies its
+ * credits (n elements: int32 if credit_bits is 32, else int64; host or
+ * device pointer) and its counters, and forgets the ticket.  In the stats,
+ * ms is the request's latency from eg_submit to completion (host clock),
+ * fixpoint_ms the device time of its batch, and the work counters are the
+ * batch's.  A request whose memory alone exceeds the budget completes with
+ * EG_ERR_OOM.  The arena must stay alive until its request is polled.
+ * eg_server_destroy waits for the running batch and drops queued requests.
+ * All calls are thread-safe.
+ */
+eg_status eg_server_create(size_t device_mem_budget, int32_t max_batch, eg_server **out);
+eg_status eg_submit(eg_server *server, eg_arena *arena, int32_t credit_bits, int64_t w_scale, int64_t w_shift,
+                    uint64_t *ticket);
+eg_status eg_poll(eg_server *server, uint64_t ticket, void *credits_out, eg_stats *st);
+eg_status eg_server_destroy(eg_server *server);
+
 /* eg_last_error -- message of the calling thread's last failure ("" if none). */
 const char *eg_last_error(void);
 

@@ -111,4 +111,12 @@ eg_status compute_bound(eg_arena *a, long long scale, long long shift, long long
 eg_status solve(eg_arena *a, int credit_bits, long long scale, long long shift, void *out, eg_stats *st,
                 cudaStream_t s, long long max_rounds);
 eg_status free_state(StateBuffers &sb);
+
+// Batched solves (eg_solve.cu), used by the server.
+struct eg_plan_impl;
+eg_status plan_create(eg_arena *ar, int count, const int32_t *part, const int64_t *w_scale, const int64_t *w_shift,
+                      int credit_bits, eg_plan_impl **out);
+eg_status plan_run(eg_plan_impl *p, void *out, eg_stats *st, cudaStream_t user, long long max_rounds);
+eg_status plan_release(eg_plan_impl *p);
+void plan_instance_info(const eg_plan_impl *p, int i, long long *offset, long long *n, long long *C, int *bits);
 }  // namespace eg

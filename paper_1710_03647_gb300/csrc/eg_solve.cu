@@ -56,6 +56,7 @@ __device__ __forceinline__ long long xchg(long long *p, long long v) {
 // w' = scale[i] * w - shift[i] with bound C[i].
 struct InstTable {
     int count;
+    int uniform_n;     // > 0: every instance holds uniform_n credits (instance = g / uniform_n)
     const int *fbase;  // count + 1
     const int *delta;
     const long long *scale;
@@ -96,6 +97,7 @@ struct View {
 __device__ __forceinline__ long long wmapv(int w, const View &v) { return v.scale * (long long)w - v.shift; }
 
 __device__ __forceinline__ int inst_of(const InstTable &I, int g) {
+    if (I.uniform_n > 0) return g / I.uniform_n;
     int lo = 0, hi = I.count;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
@@ -351,13 +353,74 @@ __device__ __forceinline__ T pull_min(const Args<T> &a, int beg, int o, const Vi
     return g;
 }
 
+// Per-warp staging of list appends: entries collect in shared memory and
+// reach the global list (items, offs, packed counter) with one atomic per
+// flush instead of one per warp step, which keeps the counters -- shared by
+// every warp of the grid -- out of the critical path.
+constexpr int STAGE = 128;
+
+struct Stager {
+    int *item;  // STAGE entries in shared memory
+    int *work;
+    int n;      // warp-uniform fill
+    unsigned long long *ctr;
+    int *items;
+    int *offs;
+};
+
+__device__ __forceinline__ void stage_flush(Stager &S) {
+    if (S.n == 0) return;
+    __syncwarp();
+    const int lane = lane_id();
+    constexpr int PER = STAGE / 32;
+    const int b = lane * PER;
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k)
+        if (b + k < S.n) sum += S.work[b + k];
+    int excl;
+    const int total = warp_exclusive(sum, excl);
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(S.ctr, ((unsigned long long)(unsigned)total << 32) | (unsigned)S.n);
+    base = __shfl_sync(FULL, base, 0);
+    const unsigned bi = (unsigned)(base & 0xffffffffu);
+    int off = (int)(base >> 32) + excl;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        if (b + k < S.n) {
+            S.items[bi + b + k] = S.item[b + k];
+            S.offs[bi + b + k] = off;
+            off += S.work[b + k];
+        }
+    }
+    __syncwarp();
+    S.n = 0;
+}
+
+// Warp-aggregated append through the stage.  Called by all 32 lanes.
+__device__ __forceinline__ void stage_append(Stager &S, bool want, unsigned item, int work) {
+    const unsigned mask = __ballot_sync(FULL, want);
+    if (mask == 0) return;
+    const int k = __popc(mask);
+    if (S.n + k > STAGE) stage_flush(S);
+    if (want) {
+        const int at = S.n + __popc(mask & ((1u << lane_id()) - 1u));
+        S.item[at] = (int)item;
+        S.work[at] = work;
+    }
+    S.n += k;
+    __syncwarp();
+}
+
 // Per-warp state of one round's push phase: the local worklist (a stack in
-// shared memory) and counters of the work done through it.
+// shared memory), the staged appends to the next round's lists, and
+// counters of the work done through the local worklist.
 template <typename T>
 struct Local {
     int *stack;
     int top;
     bool on;
+    Stager next_pull, next_push;
     unsigned long long relax, lifts, pushes;
 };
 
@@ -391,11 +454,8 @@ __device__ __forceinline__ void route(const Args<T> &a, int r, unsigned need, in
     L.top += min(__popc(lm), room);
     const bool gpull = fresh && !placed && need == NEED_PULL;
     const bool gpush = fresh && !placed && need == NEED_PUSH;
-    const int nx = (r + 1) % 3;
-    warp_append(gpull, (unsigned)p, work, &a.ctrl->pull_ctr[nx], a.pull_items[(r + 1) & 1],
-                a.pull_offs[(r + 1) & 1]);
-    warp_append(gpush, (unsigned)p, work, &a.ctrl->push_ctr[nx], a.push_items[(r + 1) & 1],
-                a.push_offs[(r + 1) & 1]);
+    stage_append(L.next_pull, gpull, (unsigned)p, work);
+    stage_append(L.next_push, gpush, (unsigned)p, work);
 }
 
 // Sends the values `val` of the window's entries over their in-edges
@@ -464,11 +524,8 @@ __device__ void drain_local(const Args<T> &a, int r, T *red, Local<T> &L) {
             const int work = !have ? 0
                              : is_pull ? __ldg(a.A.row_ptr + v + 1) - __ldg(a.A.row_ptr + v)
                                        : __ldg(a.A.rrow_ptr + v + 1) - __ldg(a.A.rrow_ptr + v);
-            const int nx = (r + 1) % 3;
-            warp_append(is_pull, (unsigned)g, work, &a.ctrl->pull_ctr[nx], a.pull_items[(r + 1) & 1],
-                        a.pull_offs[(r + 1) & 1]);
-            warp_append(is_push, (unsigned)g, work, &a.ctrl->push_ctr[nx], a.push_items[(r + 1) & 1],
-                        a.push_offs[(r + 1) & 1]);
+            stage_append(L.next_pull, is_pull, (unsigned)g, work);
+            stage_append(L.next_push, is_push, (unsigned)g, work);
             continue;
         }
         if (have) {  // unmark before reading credits
@@ -508,8 +565,7 @@ __device__ void drain_local(const Args<T> &a, int r, T *red, Local<T> &L) {
                 const unsigned bit = 1u << (g & 31);
                 gpush = !(atom_or_release(a.bits_push[(r + 1) & 1] + (g >> 5), bit) & bit);
             }
-            warp_append(gpush, (unsigned)g, qwork, &a.ctrl->push_ctr[(r + 1) % 3], a.push_items[(r + 1) & 1],
-                        a.push_offs[(r + 1) & 1]);
+            stage_append(L.next_push, gpush, (unsigned)g, qwork);
         }
         if (big || !rose) qwork = 0;
         int qo;
@@ -523,7 +579,7 @@ __device__ void drain_local(const Args<T> &a, int r, T *red, Local<T> &L) {
 // ---------------------------------------------------------------------------
 // Pull phase: lift the player-0 vertices of the pull list of round r.
 template <bool MULTI, typename T>
-__device__ void pull_phase(const Args<T> &a, int r, T *red) {
+__device__ void pull_phase(const Args<T> &a, int r, T *red, Stager &out) {
     const DevArena &A = a.A;
     const int lane = lane_id();
     const unsigned long long ctr = ld_cg(&a.ctrl->pull_ctr[r % 3]);
@@ -585,8 +641,7 @@ __device__ void pull_phase(const Args<T> &a, int r, T *red) {
                 }
             }
         }
-        warp_append(changed, (unsigned)g, pwork, &a.ctrl->push_ctr[r % 3], a.push_items[r & 1],
-                    a.push_offs[r & 1]);
+        stage_append(out, changed, (unsigned)g, pwork);
         x = stop;
         i += 32;
     }
@@ -612,6 +667,14 @@ __device__ void push_phase(const Args<T> &a, int r, T *red, Local<T> &L) {
     const int lo = gw * K;
     L.top = 0;
     L.on = a.local_windows > 0;
+    L.next_pull.n = 0;
+    L.next_pull.ctr = &a.ctrl->pull_ctr[(r + 1) % 3];
+    L.next_pull.items = a.pull_items[(r + 1) & 1];
+    L.next_pull.offs = a.pull_offs[(r + 1) & 1];
+    L.next_push.n = 0;
+    L.next_push.ctr = &a.ctrl->push_ctr[(r + 1) % 3];
+    L.next_push.items = a.push_items[(r + 1) & 1];
+    L.next_push.offs = a.push_offs[(r + 1) & 1];
     if (lo >= total) return;
     const int hi = min(total, lo + K);
 
@@ -639,18 +702,25 @@ __device__ void push_phase(const Args<T> &a, int r, T *red, Local<T> &L) {
         i += 32;
     }
     drain_local<MULTI, T>(a, r, red, L);
+    stage_flush(L.next_pull);
+    stage_flush(L.next_push);
 }
 
 // ---------------------------------------------------------------------------
 // Persistent fixpoint kernel (Algorithm 3's while-loop on the device).
 template <bool MULTI, typename T>
-__global__ void __launch_bounds__(THREADS) k_fixpoint(Args<T> a) {
+__global__ void __launch_bounds__(THREADS, 4) k_fixpoint(Args<T> a) {
     __shared__ T red_all[WARPS][32];
     __shared__ int stack_all[WARPS][LOCAL_CAP];
+    __shared__ int stage_all[WARPS][4][STAGE];
     const int wid = threadIdx.x >> 5;
     T *red = red_all[wid];
     Local<T> L;
     L.stack = stack_all[wid];
+    L.next_pull.item = stage_all[wid][0];
+    L.next_pull.work = stage_all[wid][1];
+    L.next_push.item = stage_all[wid][2];
+    L.next_push.work = stage_all[wid][3];
     L.top = 0;
     L.on = false;
     L.relax = L.lifts = L.pushes = 0;
@@ -667,7 +737,10 @@ __global__ void __launch_bounds__(THREADS) k_fixpoint(Args<T> a) {
         }
         const unsigned long long pc = ld_cg(&c->pull_ctr[r % 3]);
         if ((pc & 0xffffffffu) != 0) {
-            pull_phase<MULTI, T>(a, r, red);
+            Stager out{L.next_push.item, L.next_push.work, 0, &c->push_ctr[r % 3], a.push_items[r & 1],
+                       a.push_offs[r & 1]};
+            pull_phase<MULTI, T>(a, r, red, out);
+            stage_flush(out);
             if (!grid_barrier(c, gridDim.x, gen, BARRIER_LIMIT_NS)) break;
         }
         const unsigned long long qc = ld_cg(&c->push_ctr[r % 3]);
@@ -851,7 +924,7 @@ static eg_status launch_solve(eg_arena *ar, StateBuffers &sb, const WeightView &
                               long long max_rounds) {
     Launch L{ar->local_windows, ar->local_maxdeg, ar->warm_start, ar->seed_max_pairs, max_rounds};
     EG_CUDA_TRY(cudaEventRecord(ar->ev0, s));
-    InstTable none{1, nullptr, nullptr, nullptr, nullptr, nullptr};
+    InstTable none{1, 0, nullptr, nullptr, nullptr, nullptr, nullptr};
     eg_status rc = enqueue_solve<false, T>(ar->d, W, none, ar->n, sb, L, ar->device, s, ar->evk);
     if (rc != EG_OK) return rc;
     EG_CUDA_TRY(cudaEventRecord(ar->ev1, s));
@@ -972,7 +1045,10 @@ struct eg_plan_impl {
     bool graph_failed = false;
 };
 
-static eg_status plan_destroy(eg_plan_impl *p) {
+eg_status plan_release(eg_plan_impl *p);
+static eg_status plan_destroy(eg_plan_impl *p) { return plan_release(p); }
+
+eg_status plan_release(eg_plan_impl *p) {
     if (!p) return EG_OK;
     if (p->graph) cudaGraphExecDestroy(p->graph);
     free_state(p->sb);
@@ -1072,7 +1148,10 @@ eg_status plan_create(eg_arena *ar, int count, const int32_t *part, const int64_
     PTRY(cudaMemcpyAsync(d_scale, p->scale.data(), count * 8, cudaMemcpyHostToDevice, s));
     PTRY(cudaMemcpyAsync(d_shift, p->shift.data(), count * 8, cudaMemcpyHostToDevice, s));
     PTRY(cudaMemsetAsync(d_accC, 0, (size_t)2 * count * 8, s));
-    p->I = InstTable{count, d_fbase, d_delta, d_scale, d_shift, d_C};
+    int uniform = p->n_of[0];
+    for (int i = 1; i < count; ++i)
+        if (p->n_of[i] != uniform) uniform = 0;
+    p->I = InstTable{count, uniform, d_fbase, d_delta, d_scale, d_shift, d_C};
     const int sms = num_sms(ar->device);
     k_bound_inst<<<(int)std::min<long long>((nf + 255) / 256, (long long)sms * 32), 256, 0, s>>>(
         ar->d, p->I, (int)nf, d_accC, d_accW);
@@ -1117,6 +1196,13 @@ static eg_status plan_enqueue(eg_plan_impl *p, const Launch &L, cudaStream_t s, 
     if (rc != EG_OK) return rc;
     EG_CUDA_TRY(cudaMemcpyAsync(p->host_ctrl, p->sb.d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     return EG_OK;
+}
+
+void plan_instance_info(const eg_plan_impl *p, int i, long long *offset, long long *n, long long *C, int *bits) {
+    if (offset) *offset = p->fbase[i];
+    if (n) *n = p->n_of[i];
+    if (C) *C = p->C[i];
+    if (bits) *bits = p->bits_alone[i];
 }
 
 eg_status plan_run(eg_plan_impl *p, void *out, eg_stats *st, cudaStream_t user, long long max_rounds) {
@@ -1393,7 +1479,7 @@ static eg_status solve_noalloc(eg_arena *ar, int credit_bits, long long scale, l
 
     const WeightView W{scale, shift, C};
     const Launch L{ar->local_windows, ar->local_maxdeg, ar->warm_start, ar->seed_max_pairs, max_rounds};
-    InstTable none{1, nullptr, nullptr, nullptr, nullptr, nullptr};
+    InstTable none{1, 0, nullptr, nullptr, nullptr, nullptr, nullptr};
     EG_CUDA_TRY(cudaEventRecord(ar->ev0, s));
     rc = credit_bits == 32 ? enqueue_solve<false, int>(ar->d, W, none, ar->n, sb, L, device, s, ar->evk)
                            : enqueue_solve<false, long long>(ar->d, W, none, ar->n, sb, L, device, s, ar->evk);

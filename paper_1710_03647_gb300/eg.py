@@ -69,6 +69,10 @@ SIGNATURES = {
     "eg_plan_run": (_I32, [_P, _P, ctypes.POINTER(eg_stats), _P, _I64]),
     "eg_plan_destroy": (_I32, [_P]),
     "eg_solve_credit_noalloc": (_I32, [_P, _I32, _I64, _I64, _P, ctypes.POINTER(eg_stats), _P, _I64]),
+    "eg_server_create": (_I32, [ctypes.c_size_t, _I32, ctypes.POINTER(_P)]),
+    "eg_submit": (_I32, [_P, _P, _I32, _I64, _I64, ctypes.POINTER(ctypes.c_uint64)]),
+    "eg_poll": (_I32, [_P, ctypes.c_uint64, _P, ctypes.POINTER(eg_stats)]),
+    "eg_server_destroy": (_I32, [_P]),
     "eg_last_error": (ctypes.c_char_p, []),
     "eg_version": (ctypes.c_char_p, []),
 }
@@ -312,3 +316,30 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def eg_server_create(device_mem_budget: int, max_batch: int):
+    out = _P()
+    _check(load().eg_server_create(device_mem_budget, max_batch, ctypes.byref(out)))
+    return out.value
+
+
+def eg_submit(server, arena, credit_bits=0, w_scale=1, w_shift=0) -> int:
+    t = ctypes.c_uint64()
+    _check(load().eg_submit(server, arena, credit_bits, w_scale, w_shift, ctypes.byref(t)))
+    return t.value
+
+
+def eg_poll(server, ticket, credits_out=None):
+    """(status, eg_stats); status EG_PENDING until the request is done.
+    Errors of the request come back as the status (not raised)."""
+    st = eg_stats()
+    ptr = None
+    if credits_out is not None:
+        ptr = credits_out.ctypes.data if isinstance(credits_out, np.ndarray) else _addr(credits_out, None)
+    rc = load().eg_poll(server, ticket, ptr, ctypes.byref(st))
+    return rc, st
+
+
+def eg_server_destroy(server) -> None:
+    _check(load().eg_server_destroy(server))

@@ -1,0 +1,140 @@
+"""GPU tests of the request loop (eg_server_create / eg_submit / eg_poll):
+every request's credits are the same alone and in the mix, including
+requests submitted from several threads while earlier batches run."""
+from __future__ import annotations
+
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1710_03647_gb300 import eg, gen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    eg.load()
+
+
+def wait(server, ticket, out=None, timeout=60.0):
+    t0 = time.time()
+    while True:
+        rc, st = eg.eg_poll(server, ticket, out)
+        if rc != eg.EG_PENDING:
+            return rc, st
+        if time.time() - t0 > timeout:
+            raise TimeoutError(ticket)
+        time.sleep(0.001)
+
+
+def alone(handle, bits, scale, shift, n):
+    out = np.empty(n, dtype=np.int32 if bits == 32 else np.int64)
+    eg.eg_solve_credit(handle, bits, scale, shift, out)
+    return out
+
+
+def games():
+    return [gen.config(1, 1), gen.varied_game(3000, 2, 16, 500, seed=4), gen.rmat_game(12, 8, seed=2),
+            gen.grid_game(30, 30, seed=5), gen.tiny_game(40, 4, -3, 3, seed=9), gen.uniform_game(5000, 3, -20, 20, 6)]
+
+
+def test_mix_equals_alone():
+    gs = games()
+    arenas = [eg.Arena(g) for g in gs]
+    server = eg.eg_server_create(8 << 30, 16)
+    try:
+        reqs = []
+        for i, (g, a) in enumerate(zip(gs, arenas)):
+            for bits, scale, shift in ((0, 1, 0), (32, 1, 0), (64, 256, (i - 2) * 100)):
+                reqs.append((i, bits, scale, shift, eg.eg_submit(server, a.handle, bits, scale, shift)))
+        for i, bits, scale, shift, t in reqs:
+            out = np.empty(gs[i].n, dtype=np.int32 if bits == 32 else np.int64)
+            rc, st = wait(server, t, out)
+            assert rc == eg.EG_OK, (i, bits, rc, eg.eg_last_error())
+            np.testing.assert_array_equal(out, alone(arenas[i].handle, bits, scale, shift, gs[i].n))
+            assert st.ms > 0
+        # one more check against the oracle itself
+        f, _ = oracle.solve(gs[2].n, gs[2].row_ptr, gs[2].col, gs[2].w, gs[2].owner_bits)
+        t = eg.eg_submit(server, arenas[2].handle, 0, 1, 0)
+        out = np.empty(gs[2].n, dtype=np.int64)
+        assert wait(server, t, out)[0] == eg.EG_OK
+        np.testing.assert_array_equal(out, f)
+    finally:
+        eg.eg_server_destroy(server)
+        for a in arenas:
+            a.close()
+
+
+def test_arrivals_from_threads_while_batches_run():
+    gs = games()
+    arenas = [eg.Arena(g) for g in gs]
+    want = {i: alone(a.handle, 0, 1, 0, g.n) for i, (g, a) in enumerate(zip(gs, arenas))}
+    server = eg.eg_server_create(8 << 30, 4)  # small batches: later arrivals join later batches
+    got, errors = [], []
+
+    def client(seed):
+        rng = np.random.default_rng(seed)
+        mine = []
+        for _ in range(12):
+            i = int(rng.integers(len(gs)))
+            mine.append((i, eg.eg_submit(server, arenas[i].handle, 0, 1, 0)))
+            time.sleep(float(rng.random()) * 0.003)
+        for i, t in mine:
+            out = np.empty(gs[i].n, dtype=np.int64)
+            rc, _ = wait(server, t, out)
+            if rc != eg.EG_OK:
+                errors.append((i, rc))
+            got.append((i, out))
+
+    try:
+        ths = [threading.Thread(target=client, args=(s,)) for s in range(3)]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join(timeout=120)
+        assert not errors
+        assert len(got) == 36
+        for i, out in got:
+            np.testing.assert_array_equal(out, want[i])
+    finally:
+        eg.eg_server_destroy(server)
+        for a in arenas:
+            a.close()
+
+
+def test_budget_and_errors():
+    small, big = gen.config(1, 3), gen.rmat_game(14, 8, seed=1)
+    a_small, a_big = eg.Arena(small), eg.Arena(big)
+    server = eg.eg_server_create(1 << 20, 8)  # 1 MiB: the small game fits, the big one does not
+    try:
+        t_big = eg.eg_submit(server, a_big.handle, 0, 1, 0)
+        t_small = eg.eg_submit(server, a_small.handle, 0, 1, 0)
+        out = np.empty(small.n, dtype=np.int64)
+        assert wait(server, t_small, out)[0] == eg.EG_OK
+        np.testing.assert_array_equal(out, alone(a_small.handle, 0, 1, 0, small.n))
+        assert wait(server, t_big)[0] == eg.EG_ERR_OOM
+        rc, _ = eg.eg_poll(server, 987654321)
+        assert rc == eg.EG_ERR_INVALID
+        with pytest.raises(eg.EGError):
+            eg.eg_submit(server, a_small.handle, 16, 1, 0)
+    finally:
+        eg.eg_server_destroy(server)
+        a_small.close()
+        a_big.close()
+
+
+def test_destroy_with_pending_requests():
+    g = gen.rmat_game(13, 8, seed=3)
+    a = eg.Arena(g)
+    server = eg.eg_server_create(4 << 30, 2)
+    for _ in range(20):
+        eg.eg_submit(server, a.handle, 0, 1, 0)
+    eg.eg_server_destroy(server)  # returns after the running batch; queued ones are dropped
+    a.close()
