@@ -151,6 +151,21 @@ eg_status eg_solve_credit(eg_arena *arena, int32_t credit_bits, int64_t w_scale,
  *     whose out-degree times in-degree exceeds this.
  *   EG_OPT_GRAPH (default 1): batched solves (eg_plan_run) replay a captured
  *     CUDA graph; 0 launches the kernels directly every run.
+ *   EG_OPT_CAP_CERTIFY (default 0; used by eg_solve_credit while
+ *     EG_OPT_WARM_START is 1): a solve first tries a trial cap
+ *     B = value * max|w'| in place of C, and only keeps the result if it can
+ *     prove it exact.  It lifts the dual game -- weights
+ *     -((n+1) w' + 1), owners swapped -- with cap (n+1) B + n; a vertex with a
+ *     finite dual value is won by player 1 (player 1 then keeps every cycle
+ *     of the play strictly negative), so it starts at TOP.  It then lifts the
+ *     game itself with cap B from those starts.  If every vertex ends finite
+ *     or proven lost, every finite credit is at most B, and a cap at or above
+ *     the largest finite credit gives the same least fixpoint as C
+ *     (Sec. 3.1), so the result is exact.  Otherwise B grows eightfold (at
+ *     most four trials), and the solve ends with cap C from the proven TOP
+ *     starts.  This turns the pseudo-polynomial climb of player-1 vertices to
+ *     C into a climb to B.  0 turns it off.  max_rounds bounds each fixpoint
+ *     launch of the sequence.
  *
  * EG_ERR_INVALID for an unknown option or a negative value.
  */
@@ -159,6 +174,7 @@ eg_status eg_solve_credit(eg_arena *arena, int32_t credit_bits, int64_t w_scale,
 #define EG_OPT_WARM_START 3
 #define EG_OPT_SEED_MAX_PAIRS 4
 #define EG_OPT_GRAPH 5
+#define EG_OPT_CAP_CERTIFY 6
 eg_status eg_set_option(eg_arena *arena, int32_t option, int64_t value);
 
 /*

@@ -101,6 +101,8 @@ struct eg_arena {
     int warm_start = 1;         // TOP on player-1 negative cycles of length <= 2 before lifting
     long long seed_max_pairs = 4096;
     int use_graph = 1;                // batched solves replay a captured graph
+    int cap_certify = 0;              // first trial cap of the certified solve, in units of max|w'| (0: off)
+    unsigned long long *aux = nullptr;  // device counters of the certified solve (4 words)
     std::vector<long long> part_ptr;  // game boundaries (empty: one game)
 };
 

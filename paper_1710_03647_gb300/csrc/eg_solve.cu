@@ -45,6 +45,9 @@ namespace eg {
 
 constexpr unsigned long long BARRIER_LIMIT_NS = 5000000000ull;  // 5 s per wait
 constexpr int LOCAL_CAP = 256;  // entries of a warp's local worklist
+#ifndef EG_FIXPOINT_MIN_BLOCKS
+#define EG_FIXPOINT_MIN_BLOCKS 4  // resident blocks per SM the fixpoint kernel's registers must allow
+#endif
 
 __device__ __forceinline__ int xchg(int *p, int v) { return atomicExch(p, v); }
 __device__ __forceinline__ long long xchg(long long *p, long long v) {
@@ -78,6 +81,7 @@ struct Args {
     unsigned *bits_pull[2];  // dedupe of the pull list of round parity k
     unsigned *bits_push[2];  // dedupe of the push list of round parity k
     const unsigned *seed_bits;  // warm start: vertices that start at TOP (or null)
+    unsigned inv;      // 1: owners swapped (the dual game of a certified solve), else 0
     T *acc;
     int *acc_done;
     Ctrl *ctrl;
@@ -175,7 +179,7 @@ __global__ void k_seed(Args<T> a, long long max_pairs, unsigned *seed_bits, unsi
     for (int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < a.nf; g += nw) {
         const View vw = view_of<MULTI>(a, g);
         const int u = g - vw.delta;
-        if (!((__ldg(A.owner_bits + (u >> 5)) >> (u & 31)) & 1u)) continue;
+        if (!(((__ldg(A.owner_bits + (u >> 5)) >> (u & 31)) & 1u) ^ a.inv)) continue;
         const int ob = __ldg(A.row_ptr + u), oe = __ldg(A.row_ptr + u + 1);
         const int ib = __ldg(A.rrow_ptr + u), ie = __ldg(A.rrow_ptr + u + 1);
         if ((long long)(oe - ob) * (long long)(ie - ib) > max_pairs) continue;
@@ -201,7 +205,8 @@ __global__ void k_seed(Args<T> a, long long max_pairs, unsigned *seed_bits, unsi
                 for (int q = 0; q < cnt; ++q) {
                     const unsigned sq = __shfl_sync(FULL, sv, q);
                     const long long wq = __shfl_sync(FULL, ws, q);
-                    if ((sq & P1_FLAG) && (int)(sq & 0x7fffffffu) == t && (int)(sq & 0x7fffffffu) != u &&
+                    if (((sq & P1_FLAG) != 0) != (a.inv != 0) && (int)(sq & 0x7fffffffu) == t &&
+                        (int)(sq & 0x7fffffffu) != u &&
                         wt + wq < 0)
                         found = true;
                 }
@@ -234,7 +239,7 @@ __global__ void __launch_bounds__(THREADS) k_init(Args<T> a) {
         if (g < a.nf) {
             const View vw = view_of<MULTI>(a, g);
             const int v = g - vw.delta;
-            const bool p1 = (__ldg(A.owner_bits + (v >> 5)) >> (v & 31)) & 1u;
+            const bool p1 = ((__ldg(A.owner_bits + (v >> 5)) >> (v & 31)) & 1u) ^ a.inv;
             T f0;
             if (a.seed_bits && ((a.seed_bits[g >> 5] >> (g & 31)) & 1u)) {
                 f0 = Cred<T>::TOP;
@@ -483,7 +488,7 @@ __device__ __forceinline__ void push_edges(const Args<T> &a, int r, int beg, int
             p = pa + wj.delta;
             const T t = ominus<T>(vj, wmapv(__ldg(a.A.rw + e), wj), wj.C);
             if (t > ld_cg(a.f + p)) {
-                if (pr & P1_FLAG) {
+                if (((pr & P1_FLAG) != 0) != (a.inv != 0)) {
                     if (t > atomicMax(a.f + p, t)) {
                         work = __ldg(a.A.rrow_ptr + pa + 1) - __ldg(a.A.rrow_ptr + pa);
                         if (work > 0) need = NEED_PUSH;
@@ -709,7 +714,7 @@ __device__ void push_phase(const Args<T> &a, int r, T *red, Local<T> &L) {
 // ---------------------------------------------------------------------------
 // Persistent fixpoint kernel (Algorithm 3's while-loop on the device).
 template <bool MULTI, typename T>
-__global__ void __launch_bounds__(THREADS, 4) k_fixpoint(Args<T> a) {
+__global__ void __launch_bounds__(THREADS, EG_FIXPOINT_MIN_BLOCKS) k_fixpoint(Args<T> a) {
     __shared__ T red_all[WARPS][32];
     __shared__ int stack_all[WARPS][LOCAL_CAP];
     __shared__ int stage_all[WARPS][4][STAGE];
@@ -855,6 +860,8 @@ static eg_status ensure_state(eg_arena *ar, int bits) {
 struct Launch {
     int local_windows, local_maxdeg, warm_start;
     long long seed_max_pairs, max_rounds;
+    bool preseeded = false;  // seed_bits already holds proven TOP starts (kept; 2-cycle seeds are added)
+    unsigned inv = 0;        // 1: owners swapped (dual game)
 };
 
 // Enqueues (warm start,) initialisation and the persistent fixpoint on
@@ -894,12 +901,15 @@ static eg_status enqueue_solve(const DevArena &A, const WeightView &W, const Ins
     a.max_rounds = L.max_rounds;
     a.local_windows = L.local_windows;
     a.local_maxdeg = L.local_maxdeg;
+    a.inv = L.inv;
     a.seed_bits = nullptr;
-    if (L.warm_start) {
-        EG_CUDA_TRY(cudaMemsetAsync(sb.d.seed_bits, 0, ((size_t)nf + 31) / 32 * 4, s));
-        const int sblocks = (int)std::min<long long>((nf + 7) / 8, (long long)sms * 32);
-        k_seed<MULTI, T><<<sblocks, 256, 0, s>>>(a, L.seed_max_pairs, sb.d.seed_bits, &sb.d.ctrl->seeded);
-        EG_CUDA_TRY(cudaGetLastError());
+    if (L.warm_start || L.preseeded) {
+        if (!L.preseeded) EG_CUDA_TRY(cudaMemsetAsync(sb.d.seed_bits, 0, ((size_t)nf + 31) / 32 * 4, s));
+        if (L.warm_start) {
+            const int sblocks = (int)std::min<long long>((nf + 7) / 8, (long long)sms * 32);
+            k_seed<MULTI, T><<<sblocks, 256, 0, s>>>(a, L.seed_max_pairs, sb.d.seed_bits, &sb.d.ctrl->seeded);
+            EG_CUDA_TRY(cudaGetLastError());
+        }
         a.seed_bits = sb.d.seed_bits;
     }
     const int init_blocks = (int)std::min<long long>((nf + THREADS - 1) / THREADS, (long long)sms * 16);
@@ -920,9 +930,7 @@ static eg_status enqueue_solve(const DevArena &A, const WeightView &W, const Ins
 }
 
 template <typename T>
-static eg_status launch_solve(eg_arena *ar, StateBuffers &sb, const WeightView &W, cudaStream_t s,
-                              long long max_rounds) {
-    Launch L{ar->local_windows, ar->local_maxdeg, ar->warm_start, ar->seed_max_pairs, max_rounds};
+static eg_status launch_solve(eg_arena *ar, StateBuffers &sb, const WeightView &W, cudaStream_t s, const Launch &L) {
     EG_CUDA_TRY(cudaEventRecord(ar->ev0, s));
     InstTable none{1, 0, nullptr, nullptr, nullptr, nullptr, nullptr};
     eg_status rc = enqueue_solve<false, T>(ar->d, W, none, ar->n, sb, L, ar->device, s, ar->evk);
@@ -936,6 +944,140 @@ __global__ void k_widen(const int *in, long long *out, int n) {
         int v = in[i];
         out[i] = v == Cred<int>::TOP ? Cred<long long>::TOP : (long long)v;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Certified trial caps.
+//
+// The least fixpoint with a cap B below C is pointwise at or above the one
+// with cap C (the capped (-) only reaches TOP sooner), so a vertex finite
+// under cap B is won by player 0.  The same holds in the dual game: weights
+// -((n+1) w' + 1), owners swapped, so that player 1 is the energy player.  A
+// vertex finite there is won by player 1 in the dual, i.e. player 1 has a
+// positional strategy under which every cycle c of the play has
+// (n+1) w'(c) + |c| <= 0, hence w'(c) < 0: player 1 wins the game itself
+// from it (Lemma "EGcycles"), so its least-EPM value is TOP.  Starting those
+// vertices at TOP stays below the least fixpoint.  When, after the capped
+// lift from those starts, every vertex is finite or proven lost, every
+// vertex player 0 wins has credit <= its capped value <= B; a cap at or above
+// the largest finite credit gives the least fixpoint of cap C (Sec. 3.1,
+// the bound M_G is only needed as an upper bound on finite credits), so the
+// capped result is exact.
+
+// Bitmap of the credits a dual solve left finite (one warp per bitmap word).
+__global__ void k_mark_finite(const long long *fd, int n, unsigned *bits, unsigned long long *count) {
+    const int lane = lane_id();
+    unsigned long long cnt = 0;
+    for (int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < n; base += gridDim.x * blockDim.x) {
+        const int g = base + lane;
+        const bool fin = g < n && fd[g] != Cred<long long>::TOP;
+        const unsigned word = __ballot_sync(FULL, fin);
+        if (lane == 0) {
+            bits[base >> 5] = word;
+            cnt += __popc(word);
+        }
+    }
+    if (lane == 0 && cnt) atomicAdd(count, cnt);
+}
+
+// Number of credits at TOP that no proof puts in W1.
+template <typename T>
+__global__ void k_count_undecided(const T *f, const unsigned *bits, int n, unsigned long long *count) {
+    unsigned long long cnt = 0;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x)
+        if (f[g] == Cred<T>::TOP && !((bits[g >> 5] >> (g & 31)) & 1u)) ++cnt;
+    for (int d = 16; d; d >>= 1) cnt += __shfl_down_sync(FULL, cnt, d);
+    if (lane_id() == 0 && cnt) atomicAdd(count, cnt);
+}
+
+// Counters summed over the fixpoint launches of one solve.
+struct Totals {
+    long long rounds = 0, lifts = 0, pushes = 0, relax = 0, enqueues = 0, seeded = 0;
+    double ms = 0, kms = 0;
+};
+
+static void add_totals(Totals &t, const eg_arena *ar) {
+    const Ctrl *hc = (const Ctrl *)ar->host_ctrl;
+    float ms = 0.f, kms = 0.f;
+    cudaEventElapsedTime(&ms, ar->ev0, ar->ev1);
+    cudaEventElapsedTime(&kms, ar->evk, ar->ev1);
+    t.rounds += (long long)hc->rounds;
+    t.lifts += (long long)hc->lifts;
+    t.pushes += (long long)hc->pushes;
+    t.relax += (long long)hc->relax;
+    t.enqueues += (long long)hc->enqueues;
+    t.seeded = (long long)hc->seeded;
+    t.ms += ms;
+    t.kms += kms;
+}
+
+// One solve run to its end on s; adds its counters and returns its device status.
+template <typename T>
+static eg_status run_phase(eg_arena *ar, StateBuffers &sb, const WeightView &W, const Launch &L, cudaStream_t s,
+                           Totals &t, int &dev) {
+    eg_status rc = launch_solve<T>(ar, sb, W, s, L);
+    if (rc != EG_OK) return rc;
+    EG_CUDA_TRY(cudaMemcpyAsync(ar->host_ctrl, sb.d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    EG_CUDA_TRY(cudaStreamSynchronize(s));
+    add_totals(t, ar);
+    dev = ((const Ctrl *)ar->host_ctrl)->status;
+    if (dev != DEV_OK) sb.dirty = true;
+    return EG_OK;
+}
+
+// Tries caps B = cap_certify * max|w'| * 8^k (k < 4).  exact: sb holds the
+// least fixpoint.  seeded: sb's seed bitmap holds proven TOP starts for a
+// final solve with cap C.
+template <typename T>
+static eg_status certify(eg_arena *ar, StateBuffers &sb, long long scale, long long shift, long long C,
+                         long long wmax, cudaStream_t s, long long max_rounds, Totals &t, int &dev, bool &exact,
+                         bool &seeded, long long &nproven) {
+    exact = seeded = false;
+    dev = DEV_OK;
+    if (ar->cap_certify <= 0 || !ar->warm_start) return EG_OK;
+    constexpr long long LIM = 1LL << 61;
+    const long long n1 = (long long)ar->n + 1;
+    // every dual weight -(n+1) (scale w - shift) - 1, and the dual cap, stay below 2^61
+    const long long inner = (scale < 0 ? -scale : scale) * std::max(1LL, ar->wmax_plain) +
+                            (shift < 0 ? -shift : shift) + 1;
+    if (inner > LIM / n1) return EG_OK;
+    if (wmax > LIM / ar->cap_certify) return EG_OK;
+    long long B = (long long)ar->cap_certify * std::max(1LL, wmax);
+    if (B >= C) return EG_OK;
+    eg_status rc = ensure_state(ar, 64);
+    if (rc != EG_OK) return rc;
+    if (!ar->aux) EG_CUDA_TRY(cudaMalloc((void **)&ar->aux, 4 * sizeof(unsigned long long)));
+    StateBuffers &sd = ar->st64;
+    const int n = ar->n;
+    const int sms = num_sms(ar->device);
+    const int wblocks = (int)std::min<long long>(((long long)n + 255) / 256, (long long)sms * 16);
+    for (int attempt = 0; attempt < 4 && B < C && B <= (LIM - n1) / n1; ++attempt, B *= 8) {
+        Launch Ld{ar->local_windows, ar->local_maxdeg, 1, ar->seed_max_pairs, max_rounds};
+        Ld.inv = 1;
+        const WeightView Wd{-n1 * scale, 1 - n1 * shift, n1 * B + (n1 - 1)};
+        rc = run_phase<long long>(ar, sd, Wd, Ld, s, t, dev);
+        if (rc != EG_OK || dev != DEV_OK) return rc;
+        EG_CUDA_TRY(cudaMemsetAsync(ar->aux, 0, 2 * sizeof(unsigned long long), s));
+        k_mark_finite<<<wblocks, 256, 0, s>>>((const long long *)sd.d.f, n, sb.d.seed_bits, ar->aux);
+        EG_CUDA_TRY(cudaGetLastError());
+        Launch Lp{ar->local_windows, ar->local_maxdeg, 1, ar->seed_max_pairs, max_rounds};
+        Lp.preseeded = true;
+        rc = run_phase<T>(ar, sb, WeightView{scale, shift, B}, Lp, s, t, dev);
+        if (rc != EG_OK || dev != DEV_OK) return rc;
+        k_count_undecided<T><<<wblocks, 256, 0, s>>>((const T *)sb.d.f, sb.d.seed_bits, n, ar->aux + 1);
+        EG_CUDA_TRY(cudaGetLastError());
+        unsigned long long h[2] = {0, 0};
+        EG_CUDA_TRY(cudaMemcpyAsync(h, ar->aux, sizeof(h), cudaMemcpyDeviceToHost, s));
+        EG_CUDA_TRY(cudaStreamSynchronize(s));
+        seeded = true;
+        nproven = (long long)h[0];
+        if (h[1] == 0) {
+            exact = true;
+            return EG_OK;
+        }
+        if (B > LIM / 8) break;
+    }
+    return EG_OK;
 }
 
 eg_status solve(eg_arena *ar, int credit_bits, long long scale, long long shift, void *out, eg_stats *st,
@@ -960,9 +1102,23 @@ eg_status solve(eg_arena *ar, int credit_bits, long long scale, long long shift,
     }
     if ((rc = ensure_state(ar, bits)) != EG_OK) return rc;
     StateBuffers &sb = bits == 32 ? ar->st32 : ar->st64;
-    WeightView W{scale, shift, C};
-    rc = bits == 32 ? launch_solve<int>(ar, sb, W, s, max_rounds) : launch_solve<long long>(ar, sb, W, s, max_rounds);
+
+    Totals tot;
+    int dev = DEV_OK;
+    bool exact = false, seeded = false;
+    long long nproven = 0;
+    rc = bits == 32 ? certify<int>(ar, sb, scale, shift, C, wmax, s, max_rounds, tot, dev, exact, seeded, nproven)
+                    : certify<long long>(ar, sb, scale, shift, C, wmax, s, max_rounds, tot, dev, exact, seeded,
+                                         nproven);
     if (rc != EG_OK) return rc;
+    const bool final_launch = dev == DEV_OK && !exact;
+    if (final_launch) {
+        Launch L{ar->local_windows, ar->local_maxdeg, ar->warm_start, ar->seed_max_pairs, max_rounds};
+        L.preseeded = seeded;
+        WeightView W{scale, shift, C};
+        rc = bits == 32 ? launch_solve<int>(ar, sb, W, s, L) : launch_solve<long long>(ar, sb, W, s, L);
+        if (rc != EG_OK) return rc;
+    }
 
     // credits out: same width, or widened to int64 when credit_bits == 0
     const int out_bits = credit_bits == 0 ? 64 : bits;
@@ -982,34 +1138,35 @@ eg_status solve(eg_arena *ar, int credit_bits, long long scale, long long shift,
     EG_CUDA_TRY(cudaMemcpyAsync(out, src, (size_t)ar->n * (out_bits / 8),
                                 dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     if (tmp) EG_CUDA_TRY(cudaFreeAsync(tmp, s));
-    EG_CUDA_TRY(cudaMemcpyAsync(ar->host_ctrl, sb.d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    if (final_launch)
+        EG_CUDA_TRY(cudaMemcpyAsync(ar->host_ctrl, sb.d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     EG_CUDA_TRY(cudaStreamSynchronize(s));
-    const Ctrl *hc = (const Ctrl *)ar->host_ctrl;
-    float ms = 0.f, kms = 0.f;
-    cudaEventElapsedTime(&ms, ar->ev0, ar->ev1);
-    cudaEventElapsedTime(&kms, ar->evk, ar->ev1);
+    if (final_launch) {
+        add_totals(tot, ar);
+        dev = ((const Ctrl *)ar->host_ctrl)->status;
+    }
     eg_status result = EG_OK;
-    if (hc->status == DEV_TIMEOUT) {
+    if (dev == DEV_TIMEOUT) {
         set_error("a device-side wait exceeded its limit");
         result = EG_ERR_TIMEOUT;
         sb.dirty = true;
-    } else if (hc->status == DEV_BUDGET) {
+    } else if (dev == DEV_BUDGET) {
         set_error("round budget of %lld exhausted", max_rounds);
         result = EG_ERR_BUDGET;
         sb.dirty = true;
     }
     if (st) {
         st->C = C;
-        st->seeded = (int64_t)hc->seeded;
+        st->seeded = seeded ? nproven : tot.seeded;
         st->credit_bits = bits;
         st->status = result;
-        st->rounds = (int64_t)hc->rounds;
-        st->lifts = (int64_t)hc->lifts;
-        st->pushes = (int64_t)hc->pushes;
-        st->relaxations = (int64_t)hc->relax;
-        st->enqueues = (int64_t)hc->enqueues;
-        st->ms = ms;
-        st->fixpoint_ms = kms;
+        st->rounds = tot.rounds;
+        st->lifts = tot.lifts;
+        st->pushes = tot.pushes;
+        st->relaxations = tot.relax;
+        st->enqueues = tot.enqueues;
+        st->ms = tot.ms;
+        st->fixpoint_ms = tot.kms;
     }
     return result;
 }

@@ -267,7 +267,8 @@ def test_rmat_full_size_against_stored_oracle(name, make):
 
 SCHEDULES = [dict(warm_start=0, local_windows=0), dict(warm_start=0, local_windows=64),
              dict(warm_start=1, local_windows=0), dict(warm_start=1, local_windows=256),
-             dict(warm_start=1, local_windows=4096, local_maxdeg=8)]
+             dict(warm_start=1, local_windows=4096, local_maxdeg=8),
+             dict(warm_start=1, cap_certify=0), dict(warm_start=1, cap_certify=1, local_windows=0)]
 
 
 @pytest.mark.parametrize("sched", SCHEDULES, ids=lambda d: "-".join(f"{k}{v}" for k, v in d.items()))
@@ -304,7 +305,53 @@ def test_warm_start_under_threshold_view():
 def test_option_validation():
     a = gen.config(1, 1)
     with eg.Arena(a) as ar:
-        for opt, val in ((99, 1), (eg.EG_OPT_WARM_START, 2), (eg.EG_OPT_LOCAL_WINDOWS, -1)):
+        for opt, val in ((99, 1), (eg.EG_OPT_WARM_START, 2), (eg.EG_OPT_LOCAL_WINDOWS, -1),
+                         (eg.EG_OPT_CAP_CERTIFY, -1)):
             with pytest.raises(eg.EGError) as ei:
                 eg.eg_set_option(ar.handle, opt, val)
             assert ei.value.status == eg.EG_ERR_INVALID
+
+
+# Certified trial caps: a dual lift proves player-1 wins, a capped lift of the
+# game finishes the rest; the result must be the least fixpoint of cap C
+# whichever way the trials end (exact at the first cap, after growing it, or
+# by the final solve with cap C).
+CERT_GAMES = [lambda: gen.grid_game(32, 32, seed=1), lambda: gen.grid_game(48, 80, seed=4),
+              lambda: gen.grid_game(96, 96, seed=2), lambda: gen.rmat_game(12, 8, seed=1),
+              lambda: gen.varied_game(5000, 2, 16, 1000, seed=3), lambda: gen.uniform_game(1000, 4, -10, 10, 2),
+              lambda: gen.tiny_game(300, max_deg=4, wlo=-6, whi=6, seed=9)]
+
+
+@pytest.mark.parametrize("mult", [16, 4, 1])
+@pytest.mark.parametrize("make", CERT_GAMES, ids=["grid32", "grid48x80", "grid96", "rmat12", "varied5k",
+                                                 "uniform1k", "tiny300"])
+def test_certified_caps_exact(make, mult):
+    a = make()
+    f = ref(a)
+    for bits in (0, 64):
+        out, st = gpu(a, bits, cap_certify=mult)
+        np.testing.assert_array_equal(out, f)
+        # every vertex the dual lift proves lost is lost
+        assert 0 <= st.seeded <= int((f == TOP64).sum())
+
+
+def test_certified_caps_prove_every_loss_on_grids():
+    # at cap 16 max|w| the grid's trials end exact, so the proven set is W1
+    a = gen.grid_game(64, 64, seed=1)
+    f = ref(a)
+    out, st = gpu(a, 64, cap_certify=16)
+    np.testing.assert_array_equal(out, f)
+    assert st.seeded == int((f == TOP64).sum())
+    _, st_plain = gpu(a, 64, cap_certify=0)
+    assert st.relaxations * 20 < st_plain.relaxations
+
+
+@pytest.mark.parametrize("k", [-128, -3, 0, 2, 100])
+def test_certified_caps_under_threshold_view(k):
+    a = gen.rmat_game(11, 8, seed=7)
+    wq = gen.threshold_weights(a.w, k, 100)
+    f = ref(a, wq)
+    for mult in (16, 2):
+        out, st = gpu(a, 0, scale=256, shift=k * 100, cap_certify=mult)
+        np.testing.assert_array_equal(out, f)
+        assert st.seeded <= int((f == TOP64).sum())
