@@ -151,21 +151,24 @@ eg_status eg_solve_credit(eg_arena *arena, int32_t credit_bits, int64_t w_scale,
  *     whose out-degree times in-degree exceeds this.
  *   EG_OPT_GRAPH (default 1): batched solves (eg_plan_run) replay a captured
  *     CUDA graph; 0 launches the kernels directly every run.
- *   EG_OPT_CAP_CERTIFY (default 0; used by eg_solve_credit while
- *     EG_OPT_WARM_START is 1): a solve first tries a trial cap
- *     B = value * max|w'| in place of C, and only keeps the result if it can
- *     prove it exact.  It lifts the dual game -- weights
- *     -((n+1) w' + 1), owners swapped -- with cap (n+1) B + n; a vertex with a
- *     finite dual value is won by player 1 (player 1 then keeps every cycle
- *     of the play strictly negative), so it starts at TOP.  It then lifts the
- *     game itself with cap B from those starts.  If every vertex ends finite
- *     or proven lost, every finite credit is at most B, and a cap at or above
- *     the largest finite credit gives the same least fixpoint as C
- *     (Sec. 3.1), so the result is exact.  Otherwise B grows eightfold (at
- *     most four trials), and the solve ends with cap C from the proven TOP
- *     starts.  This turns the pseudo-polynomial climb of player-1 vertices to
- *     C into a climb to B.  0 turns it off.  max_rounds bounds each fixpoint
- *     launch of the sequence.
+ *   EG_OPT_CAP_CERTIFY (default 4; used by eg_solve_credit while
+ *     EG_OPT_WARM_START is 1): certified trial caps for games the cap-C
+ *     lifting is slow on.  A trial lifts the dual game -- weights
+ *     -(K w' + 1), owners swapped, cap (K + 1) B -- then the game itself with
+ *     cap B.  A vertex finite in the dual is won by player 1 (player 1 then
+ *     keeps every cycle of the play at negative weight), so it starts the
+ *     game's lift at TOP; a vertex finite in the game's capped lift is won by
+ *     player 0, so it starts the next dual lift at TOP.  Once every vertex is
+ *     finite or proven lost, every finite credit is at most B, and a cap at or
+ *     above the largest finite credit gives the same least fixpoint as C
+ *     (Sec. 3.1): the capped result is exact.  Trial k uses
+ *     B = value * max|w'| * 4^k and K = 8^(k+1) (at most n + 1), k < 6; if no
+ *     trial is exact the solve ends with cap C from the proven TOP starts.
+ *     This turns the pseudo-polynomial climb of player-1 vertices to C into
+ *     climbs to B.  0 turns it off.  max_rounds bounds each fixpoint launch.
+ *   EG_OPT_CERTIFY_AFTER (default 64): with certification on, a plain solve
+ *     (cap C, warm start) runs first with this round budget, and the trials
+ *     start only if it does not reach the fixpoint; 0 starts with the trials.
  *
  * EG_ERR_INVALID for an unknown option or a negative value.
  */
@@ -175,6 +178,7 @@ eg_status eg_solve_credit(eg_arena *arena, int32_t credit_bits, int64_t w_scale,
 #define EG_OPT_SEED_MAX_PAIRS 4
 #define EG_OPT_GRAPH 5
 #define EG_OPT_CAP_CERTIFY 6
+#define EG_OPT_CERTIFY_AFTER 7
 eg_status eg_set_option(eg_arena *arena, int32_t option, int64_t value);
 
 /*

@@ -268,7 +268,7 @@ static eg_status destroy(eg_arena *a) {
     free_state(a->st32);
     free_state(a->st64);
     if (a->block) cudaFree(a->block);
-    if (a->aux) cudaFree(a->aux);
+    if (a->cert_block) cudaFree(a->cert_block);
     if (a->ev0) cudaEventDestroy(a->ev0);
     if (a->ev1) cudaEventDestroy(a->ev1);
     if (a->evk) cudaEventDestroy(a->evk);
@@ -619,6 +619,7 @@ eg_status eg_set_option(eg_arena *arena, int32_t option, int64_t value) {
         break;
     case EG_OPT_SEED_MAX_PAIRS: arena->seed_max_pairs = value; break;
     case EG_OPT_CAP_CERTIFY: arena->cap_certify = (int)value; break;
+    case EG_OPT_CERTIFY_AFTER: arena->certify_after = value; break;
     case EG_OPT_GRAPH:
         if (value > 1) {
             eg::set_error("EG_OPT_GRAPH takes 0 or 1");

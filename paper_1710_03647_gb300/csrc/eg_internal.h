@@ -34,8 +34,9 @@ struct Ctrl {
     unsigned int bar_count;
     unsigned int bar_gen;
     int status;
-    int pad;
+    unsigned stop_flag;  // a slice of a resident solve ends after this round (doorbell seen)
     unsigned long long rounds, lifts, pushes, relax, enqueues, seeded;
+    long long r_next;    // round a resident solve resumes at
 };
 
 // Read-only arena data on the device (int32 offsets: m < 2^31).
@@ -101,8 +102,12 @@ struct eg_arena {
     int warm_start = 1;         // TOP on player-1 negative cycles of length <= 2 before lifting
     long long seed_max_pairs = 4096;
     int use_graph = 1;                // batched solves replay a captured graph
-    int cap_certify = 0;              // first trial cap of the certified solve, in units of max|w'| (0: off)
-    unsigned long long *aux = nullptr;  // device counters of the certified solve (4 words)
+    int cap_certify = 4;              // first trial cap of the certified solve, in units of max|w'| (0: off)
+    long long certify_after = 64;     // rounds of a first solve with cap C before the trial caps (0: none)
+    void *cert_block = nullptr;       // device memory of the certified solve:
+    unsigned long long *aux = nullptr;  //   counters (4 words)
+    unsigned *cert_w0 = nullptr;      //   bitmap of vertices proven won by player 0
+    unsigned *cert_w1 = nullptr;      //   bitmap of vertices proven won by player 1
     std::vector<long long> part_ptr;  // game boundaries (empty: one game)
 };
 
@@ -113,6 +118,42 @@ eg_status compute_bound(eg_arena *a, long long scale, long long shift, long long
 eg_status solve(eg_arena *a, int credit_bits, long long scale, long long shift, void *out, eg_stats *st,
                 cudaStream_t s, long long max_rounds);
 eg_status free_state(StateBuffers &sb);
+
+// Resident solve (eg_solve.cu), used by the server: one int64 solve state
+// over a pool of `cap` credits that holds up to `slots` games at a time.
+// Games join at a round boundary (resident_admit: weight view, warm start
+// and initial push list of the game's credit range) while others are
+// mid-solve; resident_slice runs the persistent fixpoint from the current
+// round until the doorbell rings, `rounds` rounds pass or no work is left;
+// resident_busy marks the slots that still have queued work, so the others
+// are finished.  The owner keeps A (the pool arena) valid for every range it
+// admits.
+struct Resident {
+    int device = 0;
+    int cap = 0;
+    int slots = 0;
+    DevArena A{};
+    StateBuffers sb;
+    void *block = nullptr;     // inst_id[cap], busy[slots], delta[slots], scale/shift/C[slots]
+    int *inst_id = nullptr;
+    int *busy = nullptr;
+    int *delta = nullptr;
+    long long *scale = nullptr, *shift = nullptr, *C = nullptr;
+    unsigned *bell_host = nullptr;  // mapped pinned flag; non-zero ends the running slice
+    unsigned *bell_dev = nullptr;
+    void *host_ctrl = nullptr;      // pinned copy of the control block after a slice
+    int *host_busy = nullptr;       // pinned copy of busy
+    long long r = 0;                // next round
+    int local_windows = 256, local_maxdeg = 64;
+    long long seed_max_pairs = 4096;
+};
+eg_status resident_create(Resident &R, int device, int cap, int slots, cudaStream_t s);
+void resident_free(Resident &R);
+eg_status resident_reset(Resident &R, cudaStream_t s);
+eg_status resident_admit(Resident &R, int slot, int g0, int n, long long scale, long long shift, long long C,
+                         cudaStream_t s);
+eg_status resident_slice(Resident &R, long long rounds, cudaStream_t s, int *dev_status);
+eg_status resident_busy(Resident &R, cudaStream_t s);
 
 // Batched solves (eg_solve.cu), used by the server.
 struct eg_plan_impl;

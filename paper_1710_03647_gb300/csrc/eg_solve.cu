@@ -65,6 +65,7 @@ struct InstTable {
     const long long *scale;
     const long long *shift;
     const long long *C;
+    const int *inst_id;  // non-null: instance of each credit (resident solves)
 };
 
 template <typename T>
@@ -85,7 +86,10 @@ struct Args {
     T *acc;
     int *acc_done;
     Ctrl *ctrl;
-    long long max_rounds;
+    long long max_rounds;  // round the kernel stops at (0: none)
+    long long r0;          // first round (resident solves resume where the last slice stopped)
+    int slice;             // 1: stopping at max_rounds or at the doorbell is not an error
+    const volatile unsigned *doorbell;  // resident solves: host-set flag that ends the slice
     int local_windows;  // per-warp budget of local windows per round (0: no chaining)
     int local_maxdeg;   // largest degree a vertex may have to be chained locally
 };
@@ -101,6 +105,7 @@ struct View {
 __device__ __forceinline__ long long wmapv(int w, const View &v) { return v.scale * (long long)w - v.shift; }
 
 __device__ __forceinline__ int inst_of(const InstTable &I, int g) {
+    if (I.inst_id) return __ldg(I.inst_id + g);
     if (I.uniform_n > 0) return g / I.uniform_n;
     int lo = 0, hi = I.count;
     while (hi - lo > 1) {
@@ -171,12 +176,13 @@ __global__ void k_fill(T *p, long long n, T v) {
 // for s == t; vertices with out-degree x in-degree above max_pairs are
 // skipped (the warm start is optional, missing a cycle only costs time).
 template <bool MULTI, typename T>
-__global__ void k_seed(Args<T> a, long long max_pairs, unsigned *seed_bits, unsigned long long *count) {
+__global__ void k_seed(Args<T> a, long long max_pairs, unsigned *seed_bits, unsigned long long *count, int g0,
+                       int g1) {
     const DevArena &A = a.A;
     const int lane = lane_id();
     const int nw = gridDim.x * (blockDim.x >> 5);
     unsigned found_total = 0;
-    for (int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < a.nf; g += nw) {
+    for (int g = g0 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < g1; g += nw) {
         const View vw = view_of<MULTI>(a, g);
         const int u = g - vw.delta;
         if (!(((__ldg(A.owner_bits + (u >> 5)) >> (u & 31)) & 1u) ^ a.inv)) continue;
@@ -227,16 +233,17 @@ __global__ void k_seed(Args<T> a, long long max_pairs, unsigned *seed_bits, unsi
 // at the largest for a player-0 vertex (min over edges), so it needs only the
 // per-vertex weight extremes.  It is positive exactly for the initial set L of
 // Algorithm 1 (V0 with every edge negative, V1 with some edge negative); those
-// vertices, and the warm-start ones (TOP), enter push list 0.
+// vertices, and the warm-start ones (TOP), enter the push list of the first
+// round (list counter `slot`, buffer `buf`).  Credits [g0, g1) are set.
 template <bool MULTI, typename T>
-__global__ void __launch_bounds__(THREADS) k_init(Args<T> a) {
+__global__ void __launch_bounds__(THREADS) k_init(Args<T> a, int g0, int g1, int slot, int buf) {
     const DevArena &A = a.A;
     const int nthreads = gridDim.x * blockDim.x;
-    for (int base = blockIdx.x * blockDim.x; base < a.nf; base += nthreads) {
+    for (int base = g0 + blockIdx.x * blockDim.x; base < g1; base += nthreads) {
         const int g = base + threadIdx.x;
         bool want = false;
         int work = 0;
-        if (g < a.nf) {
+        if (g < g1) {
             const View vw = view_of<MULTI>(a, g);
             const int v = g - vw.delta;
             const bool p1 = ((__ldg(A.owner_bits + (v >> 5)) >> (v & 31)) & 1u) ^ a.inv;
@@ -253,7 +260,7 @@ __global__ void __launch_bounds__(THREADS) k_init(Args<T> a) {
             work = __ldg(A.rrow_ptr + v + 1) - __ldg(A.rrow_ptr + v);
             want = f0 > T(0) && work > 0;
         }
-        warp_append(want, (unsigned)g, work, &a.ctrl->push_ctr[0], a.push_items[0], a.push_offs[0]);
+        warp_append(want, (unsigned)g, work, &a.ctrl->push_ctr[slot], a.push_items[buf], a.push_offs[buf]);
     }
 }
 
@@ -730,10 +737,13 @@ __global__ void __launch_bounds__(THREADS, EG_FIXPOINT_MIN_BLOCKS) k_fixpoint(Ar
     L.on = false;
     L.relax = L.lifts = L.pushes = 0;
     Ctrl *c = a.ctrl;
-    unsigned gen = 0;
-    for (int r = 0;; ++r) {
+    unsigned gen = ld_cg(&c->bar_gen);
+    if (blockIdx.x == 0 && threadIdx.x == 0) c->stop_flag = 0;
+    long long r_next = 0;
+    for (int r = (int)a.r0;; ++r) {
         if (a.max_rounds > 0 && r >= a.max_rounds) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&c->status, DEV_BUDGET);
+            if (blockIdx.x == 0 && threadIdx.x == 0 && !a.slice) atomicExch(&c->status, DEV_BUDGET);
+            r_next = r;
             break;
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -750,6 +760,7 @@ __global__ void __launch_bounds__(THREADS, EG_FIXPOINT_MIN_BLOCKS) k_fixpoint(Ar
         }
         const unsigned long long qc = ld_cg(&c->push_ctr[r % 3]);
         push_phase<MULTI, T>(a, r, red, L);
+        if (a.doorbell && blockIdx.x == 0 && threadIdx.x == 0 && *a.doorbell) c->stop_flag = 1;
         if (!grid_barrier(c, gridDim.x, gen, BARRIER_LIMIT_NS)) break;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             c->rounds += 1;
@@ -760,8 +771,11 @@ __global__ void __launch_bounds__(THREADS, EG_FIXPOINT_MIN_BLOCKS) k_fixpoint(Ar
         const unsigned long long np = ld_cg(&c->pull_ctr[(r + 1) % 3]);
         const unsigned long long nq = ld_cg(&c->push_ctr[(r + 1) % 3]);
         if (blockIdx.x == 0 && threadIdx.x == 0) c->enqueues += (np & 0xffffffffu) + (nq & 0xffffffffu);
+        r_next = r + 1;
         if ((np & 0xffffffffu) == 0 && (nq & 0xffffffffu) == 0) break;
+        if (a.doorbell && ld_cg(&c->stop_flag)) break;
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) c->r_next = r_next;
     if (lane_id() == 0 && (L.relax | L.lifts | L.pushes)) {
         atomicAdd(&c->relax, L.relax);
         atomicAdd(&c->lifts, L.lifts);
@@ -899,6 +913,9 @@ static eg_status enqueue_solve(const DevArena &A, const WeightView &W, const Ins
     a.acc_done = sb.d.acc_done;
     a.ctrl = sb.d.ctrl;
     a.max_rounds = L.max_rounds;
+    a.r0 = 0;
+    a.slice = 0;
+    a.doorbell = nullptr;
     a.local_windows = L.local_windows;
     a.local_maxdeg = L.local_maxdeg;
     a.inv = L.inv;
@@ -907,13 +924,14 @@ static eg_status enqueue_solve(const DevArena &A, const WeightView &W, const Ins
         if (!L.preseeded) EG_CUDA_TRY(cudaMemsetAsync(sb.d.seed_bits, 0, ((size_t)nf + 31) / 32 * 4, s));
         if (L.warm_start) {
             const int sblocks = (int)std::min<long long>((nf + 7) / 8, (long long)sms * 32);
-            k_seed<MULTI, T><<<sblocks, 256, 0, s>>>(a, L.seed_max_pairs, sb.d.seed_bits, &sb.d.ctrl->seeded);
+            k_seed<MULTI, T><<<sblocks, 256, 0, s>>>(a, L.seed_max_pairs, sb.d.seed_bits, &sb.d.ctrl->seeded, 0,
+                                                     (int)nf);
             EG_CUDA_TRY(cudaGetLastError());
         }
         a.seed_bits = sb.d.seed_bits;
     }
     const int init_blocks = (int)std::min<long long>((nf + THREADS - 1) / THREADS, (long long)sms * 16);
-    k_init<MULTI, T><<<init_blocks, THREADS, 0, s>>>(a);
+    k_init<MULTI, T><<<init_blocks, THREADS, 0, s>>>(a, 0, (int)nf, 0, 0);
     EG_CUDA_TRY(cudaGetLastError());
 
     int per_sm = 0;
@@ -952,42 +970,53 @@ __global__ void k_widen(const int *in, long long *out, int n) {
 // The least fixpoint with a cap B below C is pointwise at or above the one
 // with cap C (the capped (-) only reaches TOP sooner), so a vertex finite
 // under cap B is won by player 0.  The same holds in the dual game: weights
-// -((n+1) w' + 1), owners swapped, so that player 1 is the energy player.  A
-// vertex finite there is won by player 1 in the dual, i.e. player 1 has a
-// positional strategy under which every cycle c of the play has
-// (n+1) w'(c) + |c| <= 0, hence w'(c) < 0: player 1 wins the game itself
-// from it (Lemma "EGcycles"), so its least-EPM value is TOP.  Starting those
-// vertices at TOP stays below the least fixpoint.  When, after the capped
-// lift from those starts, every vertex is finite or proven lost, every
-// vertex player 0 wins has credit <= its capped value <= B; a cap at or above
-// the largest finite credit gives the least fixpoint of cap C (Sec. 3.1,
-// the bound M_G is only needed as an upper bound on finite credits), so the
-// capped result is exact.
+// -(K w' + 1) for some K >= 1, owners swapped, so that player 1 is the
+// energy player.  A vertex finite there is won by player 1 in the dual, i.e.
+// player 1 has a positional strategy under which every cycle c of the play
+// has K w'(c) + |c| <= 0, hence w'(c) < 0: player 1 wins the game itself
+// from it (Lemma "EGcycles"), so its least-EPM value is TOP.  Proven player-1
+// vertices start the next lift of the game at TOP, proven player-0 vertices
+// start the next lift of the dual at TOP; both starts stay below the least
+// fixpoint they lift towards.  When, after a capped lift of the game, every
+// vertex is finite or proven lost, every credit player 0 wins is at most its
+// capped value, so at most B; a cap at or above the largest finite credit
+// gives the same least fixpoint as C (Sec. 3.1 needs M_G only as an upper
+// bound on finite credits), so the capped result is exact.
+//
+// A larger K proves more (a cycle of length L and weight -s needs K >= L/s),
+// but a player-0 cycle of weight 0 climbs only L per trip in the dual, so
+// the dual's cap costs about cap/L trips: the trials start at K = 8 and a
+// small B and grow both.
 
-// Bitmap of the credits a dual solve left finite (one warp per bitmap word).
-__global__ void k_mark_finite(const long long *fd, int n, unsigned *bits, unsigned long long *count) {
+// OR of the finite credits into a bitmap (one warp per bitmap word).
+template <typename T>
+__global__ void k_mark_finite(const T *f, int n, unsigned *bits) {
     const int lane = lane_id();
-    unsigned long long cnt = 0;
     for (int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < n; base += gridDim.x * blockDim.x) {
         const int g = base + lane;
-        const bool fin = g < n && fd[g] != Cred<long long>::TOP;
+        const bool fin = g < n && f[g] != Cred<T>::TOP;
         const unsigned word = __ballot_sync(FULL, fin);
-        if (lane == 0) {
-            bits[base >> 5] = word;
-            cnt += __popc(word);
-        }
+        if (lane == 0 && word) bits[base >> 5] |= word;
     }
-    if (lane == 0 && cnt) atomicAdd(count, cnt);
 }
 
-// Number of credits at TOP that no proof puts in W1.
+// count[0] += credits at TOP that no proof puts in W1; count[1] += proven W1.
 template <typename T>
-__global__ void k_count_undecided(const T *f, const unsigned *bits, int n, unsigned long long *count) {
-    unsigned long long cnt = 0;
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x)
-        if (f[g] == Cred<T>::TOP && !((bits[g >> 5] >> (g & 31)) & 1u)) ++cnt;
-    for (int d = 16; d; d >>= 1) cnt += __shfl_down_sync(FULL, cnt, d);
-    if (lane_id() == 0 && cnt) atomicAdd(count, cnt);
+__global__ void k_count_undecided(const T *f, const unsigned *w1, int n, unsigned long long *count) {
+    unsigned long long und = 0, proven = 0;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+        const bool p = (w1[g >> 5] >> (g & 31)) & 1u;
+        proven += p;
+        und += f[g] == Cred<T>::TOP && !p;
+    }
+    for (int d = 16; d; d >>= 1) {
+        und += __shfl_down_sync(FULL, und, d);
+        proven += __shfl_down_sync(FULL, proven, d);
+    }
+    if (lane_id() == 0) {
+        if (und) atomicAdd(count, und);
+        if (proven) atomicAdd(count + 1, proven);
+    }
 }
 
 // Counters summed over the fixpoint launches of one solve.
@@ -1025,9 +1054,11 @@ static eg_status run_phase(eg_arena *ar, StateBuffers &sb, const WeightView &W, 
     return EG_OK;
 }
 
-// Tries caps B = cap_certify * max|w'| * 8^k (k < 4).  exact: sb holds the
-// least fixpoint.  seeded: sb's seed bitmap holds proven TOP starts for a
-// final solve with cap C.
+constexpr int CERT_TRIALS = 6;
+
+// Trials k = 0..5 with B = cap_certify * max|w'| * 4^k and K = 8^(k+1) (at
+// most n + 1).  exact: sb holds the least fixpoint.  seeded: sb's seed bitmap
+// holds proven TOP starts for a final solve with cap C.
 template <typename T>
 static eg_status certify(eg_arena *ar, StateBuffers &sb, long long scale, long long shift, long long C,
                          long long wmax, cudaStream_t s, long long max_rounds, Totals &t, int &dev, bool &exact,
@@ -1036,46 +1067,64 @@ static eg_status certify(eg_arena *ar, StateBuffers &sb, long long scale, long l
     dev = DEV_OK;
     if (ar->cap_certify <= 0 || !ar->warm_start) return EG_OK;
     constexpr long long LIM = 1LL << 61;
-    const long long n1 = (long long)ar->n + 1;
-    // every dual weight -(n+1) (scale w - shift) - 1, and the dual cap, stay below 2^61
+    const long long n = ar->n;
+    // |K w'| and the dual's intermediate K * scale * w stay below 2^61
     const long long inner = (scale < 0 ? -scale : scale) * std::max(1LL, ar->wmax_plain) +
                             (shift < 0 ? -shift : shift) + 1;
-    if (inner > LIM / n1) return EG_OK;
-    if (wmax > LIM / ar->cap_certify) return EG_OK;
+    if (wmax > LIM / 4 / ar->cap_certify) return EG_OK;
     long long B = (long long)ar->cap_certify * std::max(1LL, wmax);
     if (B >= C) return EG_OK;
     eg_status rc = ensure_state(ar, 64);
     if (rc != EG_OK) return rc;
-    if (!ar->aux) EG_CUDA_TRY(cudaMalloc((void **)&ar->aux, 4 * sizeof(unsigned long long)));
+    const size_t words = ((size_t)n + 31) / 32, bm = (words * 4 + 255) & ~size_t(255);
+    if (!ar->cert_block) {
+        char *blk = nullptr;
+        EG_CUDA_TRY(cudaMalloc((void **)&blk, 256 + 2 * bm));
+        ar->cert_block = blk;
+        ar->aux = (unsigned long long *)blk;
+        ar->cert_w0 = (unsigned *)(blk + 256);
+        ar->cert_w1 = (unsigned *)(blk + 256 + bm);
+    }
+    EG_CUDA_TRY(cudaMemsetAsync(ar->cert_w0, 0, 2 * bm, s));
     StateBuffers &sd = ar->st64;
-    const int n = ar->n;
     const int sms = num_sms(ar->device);
-    const int wblocks = (int)std::min<long long>(((long long)n + 255) / 256, (long long)sms * 16);
-    for (int attempt = 0; attempt < 4 && B < C && B <= (LIM - n1) / n1; ++attempt, B *= 8) {
+    const int wblocks = (int)std::min<long long>((n + 255) / 256, (long long)sms * 16);
+    long long K = std::min(8LL, n + 1);
+    for (int k = 0; k < CERT_TRIALS && B < C; ++k) {
+        if (K > LIM / inner || B > LIM / (K + 1)) break;
+        // dual: proven player-0 vertices start at TOP
+        EG_CUDA_TRY(cudaMemcpyAsync(sd.d.seed_bits, ar->cert_w0, words * 4, cudaMemcpyDeviceToDevice, s));
         Launch Ld{ar->local_windows, ar->local_maxdeg, 1, ar->seed_max_pairs, max_rounds};
         Ld.inv = 1;
-        const WeightView Wd{-n1 * scale, 1 - n1 * shift, n1 * B + (n1 - 1)};
+        Ld.preseeded = true;
+        const WeightView Wd{-K * scale, 1 - K * shift, (K + 1) * B};
         rc = run_phase<long long>(ar, sd, Wd, Ld, s, t, dev);
         if (rc != EG_OK || dev != DEV_OK) return rc;
-        EG_CUDA_TRY(cudaMemsetAsync(ar->aux, 0, 2 * sizeof(unsigned long long), s));
-        k_mark_finite<<<wblocks, 256, 0, s>>>((const long long *)sd.d.f, n, sb.d.seed_bits, ar->aux);
+        k_mark_finite<long long><<<wblocks, 256, 0, s>>>((const long long *)sd.d.f, (int)n, ar->cert_w1);
         EG_CUDA_TRY(cudaGetLastError());
+        // the game: proven player-1 vertices start at TOP
+        EG_CUDA_TRY(cudaMemcpyAsync(sb.d.seed_bits, ar->cert_w1, words * 4, cudaMemcpyDeviceToDevice, s));
         Launch Lp{ar->local_windows, ar->local_maxdeg, 1, ar->seed_max_pairs, max_rounds};
         Lp.preseeded = true;
         rc = run_phase<T>(ar, sb, WeightView{scale, shift, B}, Lp, s, t, dev);
         if (rc != EG_OK || dev != DEV_OK) return rc;
-        k_count_undecided<T><<<wblocks, 256, 0, s>>>((const T *)sb.d.f, sb.d.seed_bits, n, ar->aux + 1);
+        EG_CUDA_TRY(cudaMemsetAsync(ar->aux, 0, 2 * sizeof(unsigned long long), s));
+        k_count_undecided<T><<<wblocks, 256, 0, s>>>((const T *)sb.d.f, sb.d.seed_bits, (int)n, ar->aux);
+        EG_CUDA_TRY(cudaGetLastError());
+        k_mark_finite<T><<<wblocks, 256, 0, s>>>((const T *)sb.d.f, (int)n, ar->cert_w0);
         EG_CUDA_TRY(cudaGetLastError());
         unsigned long long h[2] = {0, 0};
         EG_CUDA_TRY(cudaMemcpyAsync(h, ar->aux, sizeof(h), cudaMemcpyDeviceToHost, s));
         EG_CUDA_TRY(cudaStreamSynchronize(s));
         seeded = true;
-        nproven = (long long)h[0];
-        if (h[1] == 0) {
+        nproven = (long long)h[1];
+        if (h[0] == 0) {
             exact = true;
             return EG_OK;
         }
-        if (B > LIM / 8) break;
+        if (B > LIM / 4) break;
+        B *= 4;
+        K = std::min(K * 8, n + 1);
     }
     return EG_OK;
 }
@@ -1107,10 +1156,27 @@ eg_status solve(eg_arena *ar, int credit_bits, long long scale, long long shift,
     int dev = DEV_OK;
     bool exact = false, seeded = false;
     long long nproven = 0;
-    rc = bits == 32 ? certify<int>(ar, sb, scale, shift, C, wmax, s, max_rounds, tot, dev, exact, seeded, nproven)
-                    : certify<long long>(ar, sb, scale, shift, C, wmax, s, max_rounds, tot, dev, exact, seeded,
-                                         nproven);
-    if (rc != EG_OK) return rc;
+    // With certification on, a first solve with cap C gets a short round
+    // budget; only a game it does not finish goes through the trial caps.
+    if (ar->cap_certify > 0 && ar->warm_start && ar->certify_after > 0 &&
+        (max_rounds == 0 || max_rounds > ar->certify_after)) {
+        Launch L{ar->local_windows, ar->local_maxdeg, 1, ar->seed_max_pairs, ar->certify_after};
+        rc = bits == 32 ? run_phase<int>(ar, sb, WeightView{scale, shift, C}, L, s, tot, dev)
+                        : run_phase<long long>(ar, sb, WeightView{scale, shift, C}, L, s, tot, dev);
+        if (rc != EG_OK) return rc;
+        if (dev == DEV_OK) {
+            exact = true;
+        } else if (dev == DEV_BUDGET) {
+            dev = DEV_OK;
+            sb.dirty = true;
+        }
+    }
+    if (!exact && dev == DEV_OK) {
+        rc = bits == 32 ? certify<int>(ar, sb, scale, shift, C, wmax, s, max_rounds, tot, dev, exact, seeded, nproven)
+                        : certify<long long>(ar, sb, scale, shift, C, wmax, s, max_rounds, tot, dev, exact, seeded,
+                                             nproven);
+        if (rc != EG_OK) return rc;
+    }
     const bool final_launch = dev == DEV_OK && !exact;
     if (final_launch) {
         Launch L{ar->local_windows, ar->local_maxdeg, ar->warm_start, ar->seed_max_pairs, max_rounds};
@@ -1513,6 +1579,179 @@ eg_status eg_plan_destroy(eg_plan *plan) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Resident solve: the state of one persistent solve over a pool of games
+// that join and leave between slices of rounds (continuous batching).
+
+namespace eg {
+
+// Clears bits [g0, g0 + n) of a bitmap.
+__global__ void k_clear_bits(unsigned *bits, int g0, int n) {
+    const int w0 = g0 >> 5, w1 = (g0 + n + 31) >> 5;
+    for (int w = w0 + blockIdx.x * blockDim.x + threadIdx.x; w < w1; w += gridDim.x * blockDim.x) {
+        const int lo = max(g0, w << 5) - (w << 5), hi = min(g0 + n, (w + 1) << 5) - (w << 5);
+        const unsigned mask = hi - lo == 32 ? FULL : (((1u << (hi - lo)) - 1u) << lo);
+        atomicAnd(bits + w, ~mask);
+    }
+}
+
+// Marks the instance of every entry of the pull and push lists of round r.
+__global__ void k_busy(const Ctrl *c, int slot, const int *pull_items, const int *push_items, const int *inst_id,
+                       int *busy) {
+    const int np = (int)(ld_cg(&c->pull_ctr[slot]) & 0xffffffffu);
+    const int nq = (int)(ld_cg(&c->push_ctr[slot]) & 0xffffffffu);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np + nq; i += gridDim.x * blockDim.x) {
+        const int g = (i < np ? ld_cg(pull_items + i) : ld_cg(push_items + (i - np))) & 0x7fffffff;
+        busy[__ldg(inst_id + g)] = 1;
+    }
+}
+
+static Args<long long> resident_args(const Resident &R) {
+    Args<long long> a;
+    a.A = R.A;
+    a.W = WeightView{1, 0, 0};
+    a.I = InstTable{R.slots, 0, nullptr, R.delta, R.scale, R.shift, R.C, R.inst_id};
+    a.nf = R.cap;
+    a.f = (long long *)R.sb.d.f;
+    for (int k = 0; k < 2; ++k) {
+        a.pull_items[k] = R.sb.d.pull_items[k];
+        a.pull_offs[k] = R.sb.d.pull_offs[k];
+        a.push_items[k] = R.sb.d.push_items[k];
+        a.push_offs[k] = R.sb.d.push_offs[k];
+        a.bits_pull[k] = R.sb.d.bits_pull[k];
+        a.bits_push[k] = R.sb.d.bits_push[k];
+    }
+    a.seed_bits = R.sb.d.seed_bits;
+    a.inv = 0;
+    a.acc = (long long *)R.sb.d.acc;
+    a.acc_done = R.sb.d.acc_done;
+    a.ctrl = R.sb.d.ctrl;
+    a.max_rounds = 0;
+    a.r0 = R.r;
+    a.slice = 1;
+    a.doorbell = R.bell_dev;
+    a.local_windows = R.local_windows;
+    a.local_maxdeg = R.local_maxdeg;
+    return a;
+}
+
+eg_status resident_reset(Resident &R, cudaStream_t s) {
+    const int sms = num_sms(R.device);
+    const size_t words = ((size_t)R.cap + 31) / 32;
+    k_fill<long long><<<sms * 4, 256, 0, s>>>((long long *)R.sb.d.acc, R.cap, Cred<long long>::TOP);
+    EG_CUDA_TRY(cudaGetLastError());
+    EG_CUDA_TRY(cudaMemsetAsync(R.sb.d.acc_done, 0, (size_t)R.cap * 4, s));
+    for (int k = 0; k < 2; ++k) {
+        EG_CUDA_TRY(cudaMemsetAsync(R.sb.d.bits_pull[k], 0, words * 4, s));
+        EG_CUDA_TRY(cudaMemsetAsync(R.sb.d.bits_push[k], 0, words * 4, s));
+    }
+    EG_CUDA_TRY(cudaMemsetAsync(R.sb.d.seed_bits, 0, words * 4, s));
+    EG_CUDA_TRY(cudaMemsetAsync(R.sb.d.ctrl, 0, sizeof(Ctrl), s));
+    R.sb.dirty = false;
+    R.r = 0;
+    EG_CUDA_TRY(cudaStreamSynchronize(s));
+    return EG_OK;
+}
+
+eg_status resident_create(Resident &R, int device, int cap, int slots, cudaStream_t s) {
+    R.device = device;
+    R.cap = cap;
+    R.slots = slots;
+    eg_status rc = alloc_state(R.sb, cap, 64);
+    if (rc != EG_OK) return rc;
+    const size_t o_busy = align_up((size_t)cap * 4), o_delta = o_busy + align_up((size_t)slots * 4);
+    const size_t o_scale = o_delta + align_up((size_t)slots * 4), o_shift = o_scale + align_up((size_t)slots * 8);
+    const size_t o_C = o_shift + align_up((size_t)slots * 8), bytes = o_C + align_up((size_t)slots * 8);
+    char *blk = nullptr;
+    EG_CUDA_TRY(cudaMalloc((void **)&blk, bytes));
+    R.block = blk;
+    R.inst_id = (int *)blk;
+    R.busy = (int *)(blk + o_busy);
+    R.delta = (int *)(blk + o_delta);
+    R.scale = (long long *)(blk + o_scale);
+    R.shift = (long long *)(blk + o_shift);
+    R.C = (long long *)(blk + o_C);
+    EG_CUDA_TRY(cudaMemsetAsync(blk, 0, bytes, s));
+    EG_CUDA_TRY(cudaHostAlloc((void **)&R.bell_host, sizeof(unsigned), cudaHostAllocMapped));
+    *(volatile unsigned *)R.bell_host = 0;
+    EG_CUDA_TRY(cudaHostGetDevicePointer((void **)&R.bell_dev, R.bell_host, 0));
+    EG_CUDA_TRY(cudaMallocHost(&R.host_ctrl, sizeof(Ctrl)));
+    EG_CUDA_TRY(cudaMallocHost((void **)&R.host_busy, (size_t)slots * 4));
+    return resident_reset(R, s);
+}
+
+void resident_free(Resident &R) {
+    free_state(R.sb);
+    if (R.block) cudaFree(R.block);
+    if (R.bell_host) cudaFreeHost(R.bell_host);
+    if (R.host_ctrl) cudaFreeHost(R.host_ctrl);
+    if (R.host_busy) cudaFreeHost(R.host_busy);
+    R.block = nullptr;
+    R.bell_host = nullptr;
+    R.host_ctrl = nullptr;
+    R.host_busy = nullptr;
+}
+
+eg_status resident_admit(Resident &R, int slot, int g0, int n, long long scale, long long shift, long long C,
+                         cudaStream_t s) {
+    const long long tab[3] = {scale, shift, C};
+    EG_CUDA_TRY(cudaMemcpyAsync(R.scale + slot, tab + 0, 8, cudaMemcpyHostToDevice, s));
+    EG_CUDA_TRY(cudaMemcpyAsync(R.shift + slot, tab + 1, 8, cudaMemcpyHostToDevice, s));
+    EG_CUDA_TRY(cudaMemcpyAsync(R.C + slot, tab + 2, 8, cudaMemcpyHostToDevice, s));
+    const int sms = num_sms(R.device);
+    const int blocks = (int)std::min<long long>((n + 255) / 256, (long long)sms * 8);
+    k_fill<int><<<blocks, 256, 0, s>>>(R.inst_id + g0, n, slot);
+    k_clear_bits<<<std::max(1, std::min((n / 32 + 255) / 256 + 1, sms * 4)), 256, 0, s>>>(R.sb.d.seed_bits, g0, n);
+    EG_CUDA_TRY(cudaGetLastError());
+    Args<long long> a = resident_args(R);
+    a.seed_bits = nullptr;
+    const int sblocks = (int)std::min<long long>((n + 7) / 8, (long long)sms * 32);
+    k_seed<true, long long><<<sblocks, 256, 0, s>>>(a, R.seed_max_pairs, R.sb.d.seed_bits, &R.sb.d.ctrl->seeded, g0,
+                                                    g0 + n);
+    EG_CUDA_TRY(cudaGetLastError());
+    a.seed_bits = R.sb.d.seed_bits;
+    const int r = (int)R.r;
+    const int iblocks = (int)std::min<long long>((n + THREADS - 1) / THREADS, (long long)sms * 16);
+    k_init<true, long long><<<iblocks, THREADS, 0, s>>>(a, g0, g0 + n, r % 3, r & 1);
+    EG_CUDA_TRY(cudaGetLastError());
+    // the host copies tab asynchronously from pageable memory: wait before it goes out of scope
+    EG_CUDA_TRY(cudaStreamSynchronize(s));
+    return EG_OK;
+}
+
+eg_status resident_slice(Resident &R, long long rounds, cudaStream_t s, int *dev_status) {
+    Args<long long> a = resident_args(R);
+    a.max_rounds = rounds > 0 ? R.r + rounds : 0;
+    int per_sm = 0;
+    EG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fixpoint<true, long long>, THREADS, 0));
+    if (per_sm < 1) {
+        set_error("fixpoint kernel cannot be resident");
+        return EG_ERR_CUDA;
+    }
+    dim3 grid(num_sms(R.device) * per_sm), block(THREADS);
+    void *args[] = {&a};
+    EG_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_fixpoint<true, long long>, grid, block, args, 0, s));
+    EG_CUDA_TRY(cudaMemcpyAsync(R.host_ctrl, R.sb.d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    EG_CUDA_TRY(cudaStreamSynchronize(s));
+    const Ctrl *hc = (const Ctrl *)R.host_ctrl;
+    *dev_status = hc->status;
+    if (hc->status == DEV_OK) R.r = hc->r_next;
+    return EG_OK;
+}
+
+eg_status resident_busy(Resident &R, cudaStream_t s) {
+    EG_CUDA_TRY(cudaMemsetAsync(R.busy, 0, (size_t)R.slots * 4, s));
+    const int r = (int)R.r;
+    k_busy<<<num_sms(R.device) * 4, 256, 0, s>>>(R.sb.d.ctrl, r % 3, R.sb.d.pull_items[r & 1],
+                                                 R.sb.d.push_items[r & 1], R.inst_id, R.busy);
+    EG_CUDA_TRY(cudaGetLastError());
+    EG_CUDA_TRY(cudaMemcpyAsync(R.host_busy, R.busy, (size_t)R.slots * 4, cudaMemcpyDeviceToHost, s));
+    EG_CUDA_TRY(cudaStreamSynchronize(s));
+    return EG_OK;
+}
+
+}  // namespace eg
 
 // ---------------------------------------------------------------------------
 // Allocation-free single solve.

@@ -150,6 +150,7 @@ EG_OPT_WARM_START = 3
 EG_OPT_SEED_MAX_PAIRS = 4
 EG_OPT_GRAPH = 5
 EG_OPT_CAP_CERTIFY = 6
+EG_OPT_CERTIFY_AFTER = 7
 
 
 def eg_solve_credit_noalloc(arena, credit_bits, w_scale, w_shift, credits_out, stream=None, max_rounds=0,
@@ -202,10 +203,11 @@ class Arena:
         _, st = eg_solve_credit(self.handle, credit_bits, w_scale, w_shift, out, stream, max_rounds)
         return out, st
 
-    def tune(self, local_windows=None, local_maxdeg=None, warm_start=None, seed_max_pairs=None, cap_certify=None):
+    def tune(self, local_windows=None, local_maxdeg=None, warm_start=None, seed_max_pairs=None, cap_certify=None,
+             certify_after=None):
         for opt, val in ((EG_OPT_LOCAL_WINDOWS, local_windows), (EG_OPT_LOCAL_MAXDEG, local_maxdeg),
                          (EG_OPT_WARM_START, warm_start), (EG_OPT_SEED_MAX_PAIRS, seed_max_pairs),
-                         (EG_OPT_CAP_CERTIFY, cap_certify)):
+                         (EG_OPT_CAP_CERTIFY, cap_certify), (EG_OPT_CERTIFY_AFTER, certify_after)):
             if val is not None:
                 eg_set_option(self.handle, opt, int(val))
 

@@ -329,7 +329,7 @@ def test_certified_caps_exact(make, mult):
     a = make()
     f = ref(a)
     for bits in (0, 64):
-        out, st = gpu(a, bits, cap_certify=mult)
+        out, st = gpu(a, bits, cap_certify=mult, certify_after=0)
         np.testing.assert_array_equal(out, f)
         # every vertex the dual lift proves lost is lost
         assert 0 <= st.seeded <= int((f == TOP64).sum())
@@ -339,11 +339,15 @@ def test_certified_caps_prove_every_loss_on_grids():
     # at cap 16 max|w| the grid's trials end exact, so the proven set is W1
     a = gen.grid_game(64, 64, seed=1)
     f = ref(a)
-    out, st = gpu(a, 64, cap_certify=16)
+    out, st = gpu(a, 64, cap_certify=16, certify_after=0)
     np.testing.assert_array_equal(out, f)
     assert st.seeded == int((f == TOP64).sum())
     _, st_plain = gpu(a, 64, cap_certify=0)
     assert st.relaxations * 20 < st_plain.relaxations
+    # the default: a short plain attempt, then the trials
+    out, st_def = gpu(a, 64)
+    np.testing.assert_array_equal(out, f)
+    assert st_def.seeded == int((f == TOP64).sum())
 
 
 @pytest.mark.parametrize("k", [-128, -3, 0, 2, 100])
@@ -352,6 +356,21 @@ def test_certified_caps_under_threshold_view(k):
     wq = gen.threshold_weights(a.w, k, 100)
     f = ref(a, wq)
     for mult in (16, 2):
-        out, st = gpu(a, 0, scale=256, shift=k * 100, cap_certify=mult)
+        out, st = gpu(a, 0, scale=256, shift=k * 100, cap_certify=mult, certify_after=0)
         np.testing.assert_array_equal(out, f)
         assert st.seeded <= int((f == TOP64).sum())
+
+
+def test_road_grid_full_size_fixpoint():
+    # 4000 x 4000 road-like grid (16M vertices, ~64.6M edges, int64 credits):
+    # too large for the oracle's Algorithm 1, so checked by properties that
+    # hold at any size: the credits satisfy every lift equation within
+    # {0..C} u {TOP}, and every TOP is a vertex the dual lift proved lost.
+    a = gen.config(3, 1)
+    out, st = gpu(a, 64)
+    assert st.status == eg.EG_OK and st.credit_bits == 64
+    code, bad = oracle.check(a.n, a.row_ptr, a.col, a.w, a.owner_bits, out, st.C)
+    assert code == 0, (code, bad)
+    ntop = int((out == TOP64).sum())
+    assert 0 < ntop < a.n
+    assert st.seeded == ntop
