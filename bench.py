@@ -165,6 +165,177 @@ def cpu_baseline():
                       f"({dt:.1f} s, {relax} edge evaluations)"}
 
 
+def ev_pair():
+    import torch
+
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def large_single_game(eg, gen, torch, dev, stream, flush):
+    """4000 x 4000 road-like grid (16M vertices, ~64.6M edges, int64 credits)
+    solved once to the exact fixpoint with the default options."""
+    a = gen.config(3, 1)
+    arena = eg.Arena(a)
+    out = torch.empty(a.n, dtype=torch.int64, device=dev)
+    res = []
+    for k in range(2):
+        with torch.cuda.stream(stream):
+            flush.fill_(k)
+        b, e = ev_pair()
+        b.record(stream)
+        _, st = eg.eg_solve_credit(arena.handle, 64, 1, 0, out, stream=stream.cuda_stream)
+        e.record(stream)
+        torch.cuda.synchronize()
+        res.append((b.elapsed_time(e), st.as_dict()))
+    arena.close()
+    ms, st = min(res, key=lambda x: x[0])
+    return {"workload": "grid4000_s1: 4000x4000 grid, 4-neighbour edges + 1% long edges, w in [-1000,1000] "
+                        "with 40% negative, owner Bernoulli(0.5), seed 1",
+            "n": a.n, "m": a.m, "credit_bits": 64, "time_to_fixpoint_ms": ms, "rounds": st["rounds"],
+            "relaxations": st["relaxations"], "lifts": st["lifts"], "proven_player1": st["seeded"],
+            "relax_per_s": st["relaxations"] / (st["fixpoint_ms"] * 1e-3),
+            "roofline_frac": algorithmic_bytes(st, 8) / (st["fixpoint_ms"] * 1e-3) / 1e9 / peaks()[0],
+            "C": st["C"], "note": "certified trial caps (default); best of 2 solves"}
+
+
+def batch_games(eg, gen, torch, dev, stream, count):
+    """`count` uneven games (n log-uniform in [1k, 200k], out-degree uniform
+    in [2, 16], weights in [-W, W], W log-uniform in [10, 10^4]): all in one
+    persistent launch (a plan over one packed arena) vs one solve per game."""
+    shapes = gen.batch_shapes(count)
+    games = [gen.batch_game(i, n, W) for i, (n, W) in enumerate(shapes)]
+    n, row_ptr, col, w, owner_bits, part_ptr = eg.pack_games(games)
+    h = eg.eg_create(n, int(row_ptr[-1]), row_ptr, col, w, owner_bits=owner_bits)
+    eg.eg_set_parts(h, part_ptr)
+    plan = eg.Plan(h, count)
+    bout = torch.empty(plan.total, dtype=torch.int64, device=dev)
+    plan.run(bout, stream=stream.cuda_stream)
+    bms = []
+    for _ in range(3):
+        b, e = ev_pair()
+        b.record(stream)
+        _, bst = plan.run(bout, stream=stream.cuda_stream)
+        e.record(stream)
+        torch.cuda.synchronize()
+        bms.append(b.elapsed_time(e))
+    batched = bout.cpu().numpy()
+    plan.close()
+    eg.eg_destroy(h)
+    # one solve (one persistent launch) per game, each game's arena resident
+    arenas = [eg.Arena(g) for g in games]
+    outs = [torch.empty(g.n, dtype=torch.int64, device=dev) for g in games]
+    for ar, o in zip(arenas[:8], outs[:8]):
+        eg.eg_solve_credit(ar.handle, 0, 1, 0, o, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    per = []
+    t0, t1 = ev_pair()
+    t0.record(stream)
+    for ar, o in zip(arenas, outs):
+        b, e = ev_pair()
+        b.record(stream)
+        eg.eg_solve_credit(ar.handle, 0, 1, 0, o, stream=stream.cuda_stream)
+        e.record(stream)
+        per.append((b, e))
+    t1.record(stream)
+    torch.cuda.synchronize()
+    total = t0.elapsed_time(t1)
+    lat = sorted(b.elapsed_time(e) for b, e in per)
+    same = all(np.array_equal(o.cpu().numpy(), batched[int(part_ptr[i]):int(part_ptr[i + 1])])
+               for i, o in enumerate(outs))
+    for ar in arenas:
+        ar.close()
+    bmed = statistics.median(bms)
+    return {"games": count, "vertices": int(n), "edges": int(row_ptr[-1]),
+            "batched_ms": bmed, "batched_games_per_s": count / (bmed * 1e-3), "batched_relaxations": bst.relaxations,
+            "per_game_total_ms": total, "per_game_games_per_s": count / (total * 1e-3),
+            "per_game_p50_ms": lat[len(lat) // 2], "per_game_p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "batched_equals_per_game": bool(same),
+            "note": "batched: one plan (one persistent launch, CUDA graph replay) over a packed arena; latency of "
+                    "every game in the batch = the batch time"}
+
+
+def serving(eg, gen, torch, dev, stream, per_rate, scales=(10, 17), seed=11):
+    """Poisson arrivals of R-MAT games (scale uniform in [lo, hi], weights in
+    [-100, 100]) served by the continuous-batching server vs. one solve at a
+    time in arrival order, at rates 0.5x-4x the serial capacity."""
+    import threading
+
+    rng = np.random.default_rng(seed)
+    pool = [gen.rmat_game(int(sc), 8, seed=100 + i) for i, sc in enumerate(range(scales[0], scales[1] + 1))]
+    arenas = [eg.Arena(g) for g in pool]
+    out = torch.empty(max(g.n for g in pool), dtype=torch.int64, device=dev)
+    # serial capacity: solves back to back
+    order = rng.integers(len(pool), size=per_rate)
+    for k in range(len(pool)):
+        eg.eg_solve_credit(arenas[k].handle, 0, 1, 0, out, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in order:
+        eg.eg_solve_credit(arenas[k].handle, 0, 1, 0, out, stream=stream.cuda_stream)
+    cap = per_rate / (time.perf_counter() - t0)
+    rows = []
+    for mult in (0.5, 1.0, 2.0, 4.0):
+        rate = mult * cap
+        gaps = rng.exponential(1.0 / rate, size=per_rate)
+        arrive = np.cumsum(gaps)
+        picks = rng.integers(len(pool), size=per_rate)
+        # serial: one solve at a time, in arrival order
+        lat_s = []
+        start = time.perf_counter()
+        for t_arr, k in zip(arrive, picks):
+            now = time.perf_counter() - start
+            if now < t_arr:
+                time.sleep(t_arr - now)
+            eg.eg_solve_credit(arenas[k].handle, 0, 1, 0, out, stream=stream.cuda_stream)
+            lat_s.append(time.perf_counter() - start - t_arr)
+        span_s = time.perf_counter() - start
+        # server: a submitting thread at the arrival times, polling here
+        server = eg.eg_server_create(16 << 30, 64)
+        tickets = [None] * per_rate
+        start = time.perf_counter()
+
+        def submit():
+            for i, (t_arr, k) in enumerate(zip(arrive, picks)):
+                now = time.perf_counter() - start
+                if now < t_arr:
+                    time.sleep(t_arr - now)
+                tickets[i] = eg.eg_submit(server, arenas[k].handle, 0, 1, 0)
+
+        th = threading.Thread(target=submit)
+        th.start()
+        lat_v, pending, done_at = [], set(range(per_rate)), 0.0
+        while pending:
+            for i in list(pending):
+                if tickets[i] is None:
+                    continue
+                rc, st = eg.eg_poll(server, tickets[i])
+                if rc == eg.EG_PENDING:
+                    continue
+                if rc != eg.EG_OK:
+                    raise RuntimeError(f"served request failed: {rc} {eg.eg_last_error()}")
+                lat_v.append(st.ms * 1e-3)
+                pending.discard(i)
+                done_at = time.perf_counter() - start
+            time.sleep(0.0002)
+        th.join()
+        eg.eg_server_destroy(server)
+
+        def pct(v, q):
+            v = sorted(v)
+            return 1e3 * v[min(len(v) - 1, int(q * len(v)))]
+
+        rows.append({"rate_x_serial_capacity": mult, "offered_games_per_s": rate,
+                     "serial_games_per_s": per_rate / span_s, "serial_p50_ms": pct(lat_s, 0.5),
+                     "serial_p99_ms": pct(lat_s, 0.99),
+                     "served_games_per_s": per_rate / done_at, "served_p50_ms": pct(lat_v, 0.5),
+                     "served_p99_ms": pct(lat_v, 0.99)})
+    for ar in arenas:
+        ar.close()
+    return {"requests_per_rate": per_rate, "game_scales": list(scales), "serial_capacity_games_per_s": cap,
+            "rates": rows, "note": "latency = completion - arrival (host clock); server: continuous batching, "
+                                   "64 slots, 16 GiB pool"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -174,6 +345,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the context solve without warm start")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched threshold-query comparison")
+    ap.add_argument("--no-large", action="store_true", help="skip the 4000x4000 grid solve")
+    ap.add_argument("--batch-games", type=int, default=512, help="games in the batched-vs-per-game comparison "
+                    "(4096 = the full workload; 0 skips it)")
+    ap.add_argument("--serve-requests", type=int, default=96, help="requests per arrival rate (0 skips serving)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -320,6 +495,14 @@ def main():
                  "roofline_frac": algorithmic_bytes(pd, s) / (pd["fixpoint_ms"] * 1e-3) / 1e9 / peaks()[0],
                  "note": "same solver, warm start off (f = 0 start as in the paper)"}
 
+    large = batch = served = None
+    if rank == 0 and not args.no_large:
+        large = large_single_game(eg, gen, torch, dev, stream, flush)
+    if rank == 0 and args.batch_games > 0:
+        batch = batch_games(eg, gen, torch, dev, stream, args.batch_games)
+    if rank == 0 and args.serve_requests > 0:
+        served = serving(eg, gen, torch, dev, stream, args.serve_requests)
+
     if rank != 0:
         arena.close()
         if pg:
@@ -350,6 +533,9 @@ def main():
         "warm_start_seeded": st0["seeded"],
         "plain": plain,
         "threshold_queries": thresholds,
+        "large_single_game": large,
+        "batch_games": batch,
+        "serving": served,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk.summary(),

@@ -246,26 +246,35 @@ eg_status eg_solve_credit_noalloc(eg_arena *arena, int32_t credit_bits, int64_t 
                                   void *credits_out, eg_stats *st, void *cuda_stream, int64_t max_rounds);
 
 /*
- * Serving.  A server owns a scheduler thread and a device memory budget.
- * eg_submit queues a solve of `arena` under the map w' = w_scale * w -
- * w_shift and returns a ticket at once.  The scheduler admits queued
- * requests in arrival order while their memory (arena copy plus solve
- * state, about 16 bytes per edge and 64 per vertex) fits the budget, up to
- * max_batch of them, packs their arenas into one device arena and solves
- * them in one batched launch (eg_plan).  Requests that arrive while a batch
- * runs wait for the next batch, which starts as soon as the running one
- * ends, so arrivals of different sizes share the device continuously.  The
- * result of every request equals eg_solve_credit on its arena alone.
+ * Serving, with continuous batching.  A server owns a scheduler thread, a
+ * pool of device memory of about device_mem_budget bytes (taken at
+ * eg_server_create: about 35% for vertex slots at 74 bytes each, 65% for
+ * edges at 16 bytes each) and one resident solve over that pool that holds up
+ * to max_batch games at once.  eg_submit queues a solve of `arena` under the
+ * map w' = w_scale * w - w_shift and returns a ticket at once.  The scheduler
+ * admits queued requests in arrival order whenever a slot is free and the
+ * game (n + 1 vertex slots, m edges) fits the free pool: it copies the arena
+ * into the pool and adds the game to the running solve at its next round, so
+ * requests that arrive while others are being solved join them on the device
+ * instead of waiting for them to finish.  The solve runs in slices of rounds
+ * that end early when a request arrives.  After each slice, every game with
+ * no work left is finished and leaves, freeing its slot and memory for the
+ * queue.  The result of every request equals eg_solve_credit on its arena
+ * alone (the games are disjoint in the pool; each has its own bound C and
+ * weight map), computed in int64.
  *
  * eg_poll returns EG_PENDING until the request is done, then copies its
  * credits (n elements: int32 if credit_bits is 32, else int64; host or
- * device pointer) and its counters, and forgets the ticket.  In the stats,
- * ms is the request's latency from eg_submit to completion (host clock),
- * fixpoint_ms the device time of its batch, and the work counters are the
- * batch's.  A request whose memory alone exceeds the budget completes with
- * EG_ERR_OOM.  The arena must stay alive until its request is polled.
- * eg_server_destroy waits for the running batch and drops queued requests.
- * All calls are thread-safe.
+ * device pointer) and its counters, and forgets the ticket.  In the stats, ms
+ * is the request's latency from eg_submit to completion (host clock),
+ * fixpoint_ms the device time of the slices it took part in, rounds the
+ * rounds it was resident, and the work counters those of the whole resident
+ * solve over that time (shared with the other games).  A request whose game
+ * can never fit the pool completes with EG_ERR_OOM; a request for int32
+ * credits whose bound does not fit completes with EG_ERR_OVERFLOW.  The arena
+ * must stay alive until its request is polled.  eg_server_destroy ends the
+ * running slice and drops queued and unfinished requests.  All calls are
+ * thread-safe.
  */
 eg_status eg_server_create(size_t device_mem_budget, int32_t max_batch, eg_server **out);
 eg_status eg_submit(eg_server *server, eg_arena *arena, int32_t credit_bits, int64_t w_scale, int64_t w_shift,

@@ -1,19 +1,26 @@
-// Request loop over many games (eg_server_create / eg_submit / eg_poll).
+// Request loop over many games (eg_server_create / eg_submit / eg_poll)
+// with continuous batching.
 //
-// A scheduler thread drains the request queue in batches: it admits queued
-// requests in arrival order while their memory fits the device budget,
-// copies their arenas into one packed device arena (vertex and edge indices
-// shifted to each game's range, so the games stay disjoint), and solves all
-// of them with one batched launch (the plan of eg_solve.cu): one instance per
-// request, each with its own bound C and weight map.  Requests submitted
-// while a batch runs wait in the queue for the next batch, which starts as
-// soon as the running one ends.
+// The server owns a pool arena sized from its device memory budget and one
+// resident solve state over it (eg_solve.cu).  A scheduler thread admits
+// queued requests in arrival order whenever a slot and room in the pool are
+// free: it copies the request's arena into a free vertex range and edge
+// range of the pool (indices shifted to the range, so the games stay
+// disjoint), computes its bound C, and appends its initial push list to the
+// round the resident solve is at.  It then runs the persistent fixpoint for
+// a slice of rounds over every resident game at once.  A slice ends after a
+// fixed number of rounds, when no work is left, or as soon as eg_submit rings
+// the doorbell, so a new request joins the running solve at the next round
+// instead of waiting for the others to finish.  After each slice, a game with
+// no entry left in the round's lists is finished: its credits are copied
+// out, its ranges and slot are freed, and waiting requests take them.
 #include <cuda_runtime.h>
 #include <string.h>
 
 #include <chrono>
 #include <condition_variable>
 #include <deque>
+#include <map>
 #include <mutex>
 #include <new>
 #include <thread>
@@ -36,15 +43,55 @@ struct Request {
     std::vector<long long> credits;  // int64 with TOP = INT64_MAX
     eg_stats st{};
     Clock::time_point submitted;
-    size_t need = 0;
+    // placement while resident
+    int slot = -1;
+    long long vb = 0, eb = 0;
+    long long C = 0;
+    long long r_admit = 0;
+    unsigned long long relax0 = 0, lifts0 = 0, pushes0 = 0, enq0 = 0;
+    double dev_ms = 0;
 };
 
-static size_t request_bytes(const eg_arena *ar) {
-    return (size_t)ar->m * 16 + (size_t)ar->n * 72 + 4096;
-}
+// First-fit allocator of index ranges, merging freed neighbours.
+struct RangeAlloc {
+    std::map<long long, long long> free_;  // start -> length
+    void init(long long cap) {
+        free_.clear();
+        if (cap > 0) free_[0] = cap;
+    }
+    long long alloc(long long len) {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < len) continue;
+            const long long st = it->first, l = it->second;
+            free_.erase(it);
+            if (l > len) free_[st + len] = l - len;
+            return st;
+        }
+        return -1;
+    }
+    void release(long long st, long long len) {
+        if (len <= 0) return;
+        auto it = free_.emplace(st, len).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+};
 
-// ---- packing kernels: game k's arrays into the pool at vertex base vb and
-// edge base eb
+// device bytes per pool vertex (arena rows, weight extremes, owner bit and
+// the int64 solve state with its lists, bitmaps and slot ids) and per edge
+constexpr size_t POOL_VERTEX_BYTES = 74;
+constexpr size_t POOL_EDGE_BYTES = 16;
+constexpr long long SLICE_ROUNDS = 32;
 
 __global__ void k_pack_rows(int *dst, const int *src, int n, int add) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i] + add;
@@ -61,20 +108,22 @@ __global__ void k_pack_rcols(unsigned *dst, const unsigned *src, int m, int add)
     }
 }
 
+// owner bits of game vertices [0, n) to pool bits [vb, vb + n); the range's
+// old bits were cleared first (k_unset_bits)
 __global__ void k_pack_owner(unsigned *dst, const unsigned *src, int n, int vb) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         if ((src[i >> 5] >> (i & 31)) & 1u) atomicOr(dst + ((vb + i) >> 5), 1u << ((vb + i) & 31));
 }
 
-__global__ void k_set_tail(int *row_ptr, int *rrow_ptr, int n, int m) {
-    row_ptr[n] = m;
-    rrow_ptr[n] = m;
+__global__ void k_unset_bits(unsigned *bits, int g0, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        atomicAnd(bits + ((g0 + i) >> 5), ~(1u << ((g0 + i) & 31)));
 }
 
 struct Server {
     int device = 0;
     size_t budget = 0;
-    int max_batch = 1;
+    int max_slots = 1;
     std::mutex mu;
     std::condition_variable cv, done_cv;
     std::deque<Request *> queue;
@@ -83,190 +132,252 @@ struct Server {
     bool stop = false;
     std::thread worker;
     cudaStream_t stream = nullptr;
-    // pool: one device block for the packed arena, one for the int64 result
-    eg_arena pool;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    // the pool: vertex slots [0, NV) and edges [0, NE); a game of n vertices
+    // takes n + 1 vertex slots (its last row offset sits in the extra one)
+    long long NV = 0, NE = 0;
     void *pool_block = nullptr;
-    size_t pool_bytes = 0;
-    long long *result = nullptr;
-    size_t result_cap = 0;
-    long long *host_result = nullptr;
-    size_t host_cap = 0;
+    DevArena pool{};
+    RangeAlloc vfree, efree;
+    std::vector<int> free_slots;
+    std::vector<Request *> active;  // by slot
+    int nactive = 0;
+    Resident R;
+    long long *stage = nullptr;  // pinned staging of finished credits
+    size_t stage_cap = 0;
 };
 
 static size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 
-static eg_status ensure_pool(Server *S, long long n, long long m) {
-    const size_t words = ((size_t)n + 31) / 32;
-    const size_t need = 2 * up256(((size_t)n + 1) * 4) + 4 * up256((size_t)m * 4) + up256(words * 4) +
-                        2 * up256((size_t)n * 4);
-    if (need > S->pool_bytes) {
-        if (S->pool_block) cudaFree(S->pool_block);
-        S->pool_block = nullptr;
-        S->pool_bytes = 0;
-        EG_CUDA_TRY(cudaMalloc(&S->pool_block, need));
-        S->pool_bytes = need;
-    }
+static eg_status create_pool(Server *S) {
+    const long long NV = S->NV, NE = S->NE;
+    const size_t words = ((size_t)NV + 31) / 32;
+    const size_t bytes = 2 * up256(((size_t)NV + 1) * 4) + 4 * up256((size_t)NE * 4) + up256(words * 4) +
+                         2 * up256((size_t)NV * 4);
+    EG_CUDA_TRY(cudaMalloc(&S->pool_block, bytes));
+    EG_CUDA_TRY(cudaMemsetAsync(S->pool_block, 0, bytes, S->stream));
     char *b = (char *)S->pool_block;
     size_t off = 0;
-    auto take = [&](size_t bytes) {
+    auto take = [&](size_t n) {
         char *p = b + off;
-        off += up256(bytes);
+        off += up256(n);
         return p;
     };
-    DevArena &d = S->pool.d;
-    d.n = (int)n;
-    d.m = (int)m;
-    d.row_ptr = (int *)take(((size_t)n + 1) * 4);
-    d.col = (int *)take((size_t)m * 4);
-    d.w = (int *)take((size_t)m * 4);
-    d.rrow_ptr = (int *)take(((size_t)n + 1) * 4);
-    d.rcol = (unsigned *)take((size_t)m * 4);
-    d.rw = (int *)take((size_t)m * 4);
+    DevArena &d = S->pool;
+    d.n = (int)NV;
+    d.m = (int)NE;
+    d.row_ptr = (int *)take(((size_t)NV + 1) * 4);
+    d.col = (int *)take((size_t)NE * 4);
+    d.w = (int *)take((size_t)NE * 4);
+    d.rrow_ptr = (int *)take(((size_t)NV + 1) * 4);
+    d.rcol = (unsigned *)take((size_t)NE * 4);
+    d.rw = (int *)take((size_t)NE * 4);
     d.owner_bits = (unsigned *)take(words * 4);
-    d.wmin = (int *)take((size_t)n * 4);
-    d.wmax = (int *)take((size_t)n * 4);
-    S->pool.n = (int)n;
-    S->pool.m = (int)m;
-    if ((size_t)n > S->result_cap) {
-        if (S->result) cudaFree(S->result);
-        S->result = nullptr;
-        S->result_cap = 0;
-        EG_CUDA_TRY(cudaMalloc((void **)&S->result, (size_t)n * 8));
-        S->result_cap = (size_t)n;
+    d.wmin = (int *)take((size_t)NV * 4);
+    d.wmax = (int *)take((size_t)NV * 4);
+    eg_status rc = resident_create(S->R, S->device, (int)NV, S->max_slots, S->stream);
+    if (rc != EG_OK) return rc;
+    S->R.A = S->pool;
+    S->vfree.init(NV);
+    S->efree.init(NE);
+    S->free_slots.clear();
+    for (int k = S->max_slots - 1; k >= 0; --k) S->free_slots.push_back(k);
+    S->active.assign(S->max_slots, nullptr);
+    return EG_OK;
+}
+
+// Copies the request's arena into its pool ranges and joins it to the solve.
+static eg_status place(Server *S, Request *r) {
+    cudaStream_t s = S->stream;
+    const DevArena &a = r->ar->d;
+    DevArena &d = S->pool;
+    const int vb = (int)r->vb, eb = (int)r->eb;
+    const int g1 = (int)std::min<long long>((a.n + 256) / 256, 4096);
+    const int g2 = (int)std::min<long long>((a.m + 255) / 256, 8192);
+    k_pack_rows<<<g1, 256, 0, s>>>((int *)d.row_ptr + vb, a.row_ptr, a.n + 1, eb);
+    k_pack_rows<<<g1, 256, 0, s>>>((int *)d.rrow_ptr + vb, a.rrow_ptr, a.n + 1, eb);
+    k_pack_cols<<<g2, 256, 0, s>>>((int *)d.col + eb, a.col, a.m, vb);
+    k_pack_rcols<<<g2, 256, 0, s>>>((unsigned *)d.rcol + eb, a.rcol, a.m, vb);
+    k_unset_bits<<<g1, 256, 0, s>>>((unsigned *)d.owner_bits, vb, a.n + 1);
+    k_pack_owner<<<g1, 256, 0, s>>>((unsigned *)d.owner_bits, a.owner_bits, a.n, vb);
+    EG_CUDA_TRY(cudaGetLastError());
+    EG_CUDA_TRY(cudaMemcpyAsync((int *)d.w + eb, a.w, (size_t)a.m * 4, cudaMemcpyDeviceToDevice, s));
+    EG_CUDA_TRY(cudaMemcpyAsync((int *)d.rw + eb, a.rw, (size_t)a.m * 4, cudaMemcpyDeviceToDevice, s));
+    EG_CUDA_TRY(cudaMemcpyAsync((int *)d.wmin + vb, a.wmin, (size_t)a.n * 4, cudaMemcpyDeviceToDevice, s));
+    EG_CUDA_TRY(cudaMemcpyAsync((int *)d.wmax + vb, a.wmax, (size_t)a.n * 4, cudaMemcpyDeviceToDevice, s));
+    long long C = 0, wmax = 0;
+    eg_status rc = compute_bound(r->ar, r->scale, r->shift, &C, &wmax, s);
+    if (rc != EG_OK) return rc;
+    if (r->credit_bits == 32 && C + wmax > 0x7fffffffLL - 1) {
+        set_error("int32 credits cannot hold C + max|w'| = %lld", C + wmax);
+        return EG_ERR_OVERFLOW;
     }
-    if ((size_t)n > S->host_cap) {
-        if (S->host_result) cudaFreeHost(S->host_result);
-        S->host_result = nullptr;
-        S->host_cap = 0;
-        EG_CUDA_TRY(cudaMallocHost((void **)&S->host_result, (size_t)n * 8));
-        S->host_cap = (size_t)n;
+    r->C = C;
+    rc = resident_admit(S->R, r->slot, vb, a.n, r->scale, r->shift, C, s);
+    if (rc != EG_OK) return rc;
+    const Ctrl *hc = (const Ctrl *)S->R.host_ctrl;
+    r->r_admit = S->R.r;
+    r->relax0 = hc->relax;
+    r->lifts0 = hc->lifts;
+    r->pushes0 = hc->pushes;
+    r->enq0 = hc->enqueues;
+    return EG_OK;
+}
+
+static void release(Server *S, Request *r) {
+    S->vfree.release(r->vb, (long long)r->ar->n + 1);
+    S->efree.release(r->eb, r->ar->m);
+    if (r->slot >= 0) {
+        S->active[r->slot] = nullptr;
+        S->free_slots.push_back(r->slot);
+        r->slot = -1;
+    }
+}
+
+// Marks requests done (under the lock) and wakes pollers.
+static void complete(Server *S, std::vector<Request *> &fin) {
+    if (fin.empty()) return;
+    const auto now = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (Request *r : fin) {
+            r->st.status = r->status;
+            r->st.ms = std::chrono::duration<double, std::milli>(now - r->submitted).count();
+            r->done = true;
+        }
+    }
+    S->done_cv.notify_all();
+    fin.clear();
+}
+
+static eg_status harvest(Server *S, std::vector<Request *> &fin) {
+    eg_status rc = resident_busy(S->R, S->stream);
+    if (rc != EG_OK) return rc;
+    std::vector<Request *> ready;
+    size_t total = 0;
+    for (int k = 0; k < S->max_slots; ++k) {
+        Request *r = S->active[k];
+        if (r && !S->R.host_busy[k]) {
+            ready.push_back(r);
+            total += (size_t)r->ar->n;
+        }
+    }
+    if (ready.empty()) return EG_OK;
+    if (total > S->stage_cap) {
+        if (S->stage) cudaFreeHost(S->stage);
+        S->stage = nullptr;
+        S->stage_cap = 0;
+        EG_CUDA_TRY(cudaMallocHost((void **)&S->stage, total * 8));
+        S->stage_cap = total;
+    }
+    size_t off = 0;
+    for (Request *r : ready) {
+        EG_CUDA_TRY(cudaMemcpyAsync(S->stage + off, (const long long *)S->R.sb.d.f + r->vb, (size_t)r->ar->n * 8,
+                                    cudaMemcpyDeviceToHost, S->stream));
+        off += (size_t)r->ar->n;
+    }
+    EG_CUDA_TRY(cudaStreamSynchronize(S->stream));
+    const Ctrl *hc = (const Ctrl *)S->R.host_ctrl;
+    off = 0;
+    for (Request *r : ready) {
+        r->credits.assign(S->stage + off, S->stage + off + r->ar->n);
+        off += (size_t)r->ar->n;
+        r->st = eg_stats{};
+        r->st.C = r->C;
+        r->st.credit_bits = r->credit_bits == 32 ? 32 : 64;
+        r->st.rounds = S->R.r - r->r_admit;
+        r->st.lifts = (int64_t)(hc->lifts - r->lifts0);
+        r->st.pushes = (int64_t)(hc->pushes - r->pushes0);
+        r->st.relaxations = (int64_t)(hc->relax - r->relax0);
+        r->st.enqueues = (int64_t)(hc->enqueues - r->enq0);
+        r->st.fixpoint_ms = r->dev_ms;
+        r->status = EG_OK;
+        release(S, r);
+        --S->nactive;
+        fin.push_back(r);
     }
     return EG_OK;
 }
 
-static eg_status run_batch(Server *S, std::vector<Request *> &batch) {
-    long long n = 0, m = 0;
-    for (Request *r : batch) {
-        n += r->ar->n;
-        m += r->ar->m;
+static void fail_active(Server *S, eg_status rc, std::vector<Request *> &fin) {
+    for (int k = 0; k < S->max_slots; ++k) {
+        Request *r = S->active[k];
+        if (!r) continue;
+        r->status = rc;
+        release(S, r);
+        --S->nactive;
+        fin.push_back(r);
     }
-    if (n >= (1LL << 31) - 1 || m >= (1LL << 31) - 1) {
-        set_error("batch too large for int32 indices");
-        return EG_ERR_INVALID;
-    }
-    eg_status rc = ensure_pool(S, n, m);
-    if (rc != EG_OK) return rc;
-    cudaStream_t s = S->stream;
-    DevArena &d = S->pool.d;
-    EG_CUDA_TRY(cudaMemsetAsync((void *)d.owner_bits, 0, (((size_t)n + 31) / 32) * 4, s));
-    S->pool.part_ptr.assign(1, 0);
-    long long vb = 0, eb = 0;
-    for (Request *r : batch) {
-        const DevArena &a = r->ar->d;
-        const int g1 = (int)std::min<long long>((a.n + 255) / 256, 4096);
-        const int g2 = (int)std::min<long long>((a.m + 255) / 256, 8192);
-        k_pack_rows<<<g1, 256, 0, s>>>((int *)d.row_ptr + vb, a.row_ptr, a.n, (int)eb);
-        k_pack_rows<<<g1, 256, 0, s>>>((int *)d.rrow_ptr + vb, a.rrow_ptr, a.n, (int)eb);
-        k_pack_cols<<<g2, 256, 0, s>>>((int *)d.col + eb, a.col, a.m, (int)vb);
-        k_pack_rcols<<<g2, 256, 0, s>>>((unsigned *)d.rcol + eb, a.rcol, a.m, (int)vb);
-        k_pack_owner<<<g1, 256, 0, s>>>((unsigned *)d.owner_bits, a.owner_bits, a.n, (int)vb);
-        EG_CUDA_TRY(cudaGetLastError());
-        EG_CUDA_TRY(cudaMemcpyAsync((int *)d.w + eb, a.w, (size_t)a.m * 4, cudaMemcpyDeviceToDevice, s));
-        EG_CUDA_TRY(cudaMemcpyAsync((int *)d.rw + eb, a.rw, (size_t)a.m * 4, cudaMemcpyDeviceToDevice, s));
-        EG_CUDA_TRY(cudaMemcpyAsync((int *)d.wmin + vb, a.wmin, (size_t)a.n * 4, cudaMemcpyDeviceToDevice, s));
-        EG_CUDA_TRY(cudaMemcpyAsync((int *)d.wmax + vb, a.wmax, (size_t)a.n * 4, cudaMemcpyDeviceToDevice, s));
-        vb += a.n;
-        eb += a.m;
-        S->pool.part_ptr.push_back(vb);
-    }
-    k_set_tail<<<1, 1, 0, s>>>((int *)d.row_ptr, (int *)d.rrow_ptr, (int)n, (int)m);
-    EG_CUDA_TRY(cudaGetLastError());
-    EG_CUDA_TRY(cudaStreamSynchronize(s));
-
-    const int k = (int)batch.size();
-    std::vector<int32_t> part(k);
-    std::vector<int64_t> sc(k), sh(k);
-    bool want64 = false;
-    for (int i = 0; i < k; ++i) {
-        part[i] = i;
-        sc[i] = batch[i]->scale;
-        sh[i] = batch[i]->shift;
-        want64 = want64 || batch[i]->credit_bits == 64;
-    }
-    eg_plan_impl *plan = nullptr;
-    rc = plan_create(&S->pool, k, part.data(), sc.data(), sh.data(), want64 ? 64 : 0, &plan);
-    if (rc != EG_OK) return rc;
-    eg_stats st{};
-    rc = plan_run(plan, S->result, &st, s, 0);
-    if (rc == EG_OK) {
-        cudaError_t e = cudaMemcpyAsync(S->host_result, S->result, (size_t)n * 8, cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e != cudaSuccess) {
-            set_error("result copy failed: %s", cudaGetErrorString(e));
-            rc = EG_ERR_CUDA;
-        }
-    }
-    if (rc == EG_OK) {
-        for (int i = 0; i < k; ++i) {
-            long long off = 0, len = 0, C = 0;
-            int bits_alone = 32;
-            plan_instance_info(plan, i, &off, &len, &C, &bits_alone);
-            Request *r = batch[i];
-            r->st = st;
-            r->st.C = C;
-            r->st.fixpoint_ms = st.ms;
-            if (r->credit_bits == 32 && bits_alone == 64) {
-                r->status = EG_ERR_OVERFLOW;
-                continue;
-            }
-            r->st.credit_bits = r->credit_bits == 32 ? 32 : 64;
-            r->credits.assign(S->host_result + off, S->host_result + off + len);
-        }
-    }
-    plan_release(plan);
-    return rc;
 }
 
 static void worker_main(Server *S) {
     cudaSetDevice(S->device);
+    std::vector<Request *> fin;
     for (;;) {
-        std::vector<Request *> batch;
+        std::vector<Request *> admitted;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            S->cv.wait(lk, [&] { return S->stop || !S->queue.empty(); });
-            if (S->stop) return;
-            size_t mem = 0;
-            while (!S->queue.empty() && (int)batch.size() < S->max_batch) {
+            S->cv.wait(lk, [&] { return S->stop || !S->queue.empty() || S->nactive > 0; });
+            if (S->stop) break;
+            while (!S->queue.empty() && !S->free_slots.empty()) {
                 Request *r = S->queue.front();
-                if (r->need > S->budget) {
+                const long long nv = (long long)r->ar->n + 1, m = r->ar->m;
+                if (nv > S->NV || m > S->NE) {  // can never fit the budget
                     S->queue.pop_front();
                     r->status = EG_ERR_OOM;
-                    r->st.status = EG_ERR_OOM;
-                    r->done = true;
+                    fin.push_back(r);
                     continue;
                 }
-                if (mem + r->need > S->budget && !batch.empty()) break;
+                const long long vb = S->vfree.alloc(nv);
+                if (vb < 0) break;
+                const long long eb = S->efree.alloc(m);
+                if (eb < 0) {
+                    S->vfree.release(vb, nv);
+                    break;
+                }
                 S->queue.pop_front();
-                batch.push_back(r);
-                mem += r->need;
+                r->vb = vb;
+                r->eb = eb;
+                r->slot = S->free_slots.back();
+                S->free_slots.pop_back();
+                S->active[r->slot] = r;
+                ++S->nactive;
+                admitted.push_back(r);
             }
-            if (batch.empty()) {
-                S->done_cv.notify_all();
-                continue;
+            *(volatile unsigned *)S->R.bell_host = 0;  // a later eg_submit rings again
+        }
+        for (Request *r : admitted) {
+            const eg_status rc = place(S, r);
+            if (rc != EG_OK) {
+                r->status = rc;
+                release(S, r);
+                --S->nactive;
+                fin.push_back(r);
             }
         }
-        const eg_status rc = run_batch(S, batch);
-        const auto now = Clock::now();
-        {
-            std::lock_guard<std::mutex> lk(S->mu);
-            for (Request *r : batch) {
-                if (rc != EG_OK && r->status == EG_OK) r->status = rc;
-                r->st.status = r->status;
-                r->st.ms = std::chrono::duration<double, std::milli>(now - r->submitted).count();
-                r->done = true;
-            }
+        complete(S, fin);
+        if (S->nactive == 0) continue;
+        int dev = DEV_OK;
+        cudaEventRecord(S->e0, S->stream);
+        eg_status rc = resident_slice(S->R, SLICE_ROUNDS, S->stream, &dev);
+        cudaEventRecord(S->e1, S->stream);
+        if (rc == EG_OK && dev != DEV_OK) {
+            set_error("a device-side wait exceeded its limit");
+            rc = EG_ERR_TIMEOUT;
         }
-        S->done_cv.notify_all();
+        if (rc == EG_OK) {
+            cudaEventSynchronize(S->e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, S->e0, S->e1);
+            for (Request *r : S->active)
+                if (r) r->dev_ms += ms;
+            rc = harvest(S, fin);
+        }
+        if (rc != EG_OK) {
+            fail_active(S, rc, fin);
+            resident_reset(S->R, S->stream);
+        }
+        complete(S, fin);
     }
 }
 
@@ -289,16 +400,29 @@ eg_status eg_server_create(size_t device_mem_budget, int32_t max_batch, eg_serve
         return EG_ERR_OOM;
     }
     S->budget = device_mem_budget;
-    S->max_batch = max_batch;
+    S->max_slots = max_batch;
     cudaGetDevice(&S->device);
-    S->pool.device = S->device;
-    S->pool.use_graph = 0;  // a new packing every batch: nothing to replay
+    // split the budget between vertex slots and edges in the proportion of
+    // a game with about 8 edges per vertex
+    const double vb = 0.35 * (double)device_mem_budget / eg::POOL_VERTEX_BYTES;
+    const double ebytes = 0.65 * (double)device_mem_budget / eg::POOL_EDGE_BYTES;
+    S->NV = (long long)std::min(vb, (double)((1LL << 31) - 64));
+    S->NE = (long long)std::min(ebytes, (double)((1LL << 31) - 64));
+    if (S->NV < 2 || S->NE < 1) {
+        eg::set_error("budget too small for any game");
+        delete S;
+        return EG_ERR_INVALID;
+    }
     if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreate(&S->pool.ev0) != cudaSuccess || cudaEventCreate(&S->pool.ev1) != cudaSuccess ||
-        cudaEventCreate(&S->pool.evk) != cudaSuccess || cudaMallocHost(&S->pool.host_ctrl, sizeof(eg::Ctrl)) != cudaSuccess) {
+        cudaEventCreate(&S->e0) != cudaSuccess || cudaEventCreate(&S->e1) != cudaSuccess) {
         eg::set_error("server set-up failed: %s", cudaGetErrorString(cudaGetLastError()));
         eg_server_destroy(S);
         return EG_ERR_CUDA;
+    }
+    eg_status prc = eg::create_pool(S);
+    if (prc != EG_OK) {
+        eg_server_destroy(S);
+        return prc;
     }
     try {
         S->worker = std::thread(eg::worker_main, (eg::Server *)S);
@@ -336,7 +460,6 @@ eg_status eg_submit(eg_server *S, eg_arena *arena, int32_t credit_bits, int64_t 
     r->credit_bits = credit_bits;
     r->scale = w_scale;
     r->shift = w_shift;
-    r->need = eg::request_bytes(arena);
     r->submitted = eg::Clock::now();
     {
         std::lock_guard<std::mutex> lk(S->mu);
@@ -349,6 +472,7 @@ eg_status eg_submit(eg_server *S, eg_arena *arena, int32_t credit_bits, int64_t 
         S->all[r->ticket] = r;
         S->queue.push_back(r);
         *ticket = r->ticket;
+        if (S->R.bell_host) *(volatile unsigned *)S->R.bell_host = 1;  // end the running slice early
     }
     S->cv.notify_one();
     return EG_OK;
@@ -412,22 +536,20 @@ eg_status eg_server_destroy(eg_server *S) {
     {
         std::lock_guard<std::mutex> lk(S->mu);
         S->stop = true;
+        if (S->R.bell_host) *(volatile unsigned *)S->R.bell_host = 1;
     }
     S->cv.notify_all();
     if (S->worker.joinable()) S->worker.join();
+    if (S->stream) cudaStreamSynchronize(S->stream);
     for (auto &kv : S->all) delete kv.second;
     S->all.clear();
     S->queue.clear();
+    eg::resident_free(S->R);
     if (S->pool_block) cudaFree(S->pool_block);
-    if (S->result) cudaFree(S->result);
-    if (S->host_result) cudaFreeHost(S->host_result);
+    if (S->stage) cudaFreeHost(S->stage);
     if (S->stream) cudaStreamDestroy(S->stream);
-    if (S->pool.ev0) cudaEventDestroy(S->pool.ev0);
-    if (S->pool.ev1) cudaEventDestroy(S->pool.ev1);
-    if (S->pool.evk) cudaEventDestroy(S->pool.evk);
-    if (S->pool.host_ctrl) cudaFreeHost(S->pool.host_ctrl);
-    S->pool.host_ctrl = nullptr;
-    S->pool.ev0 = S->pool.ev1 = S->pool.evk = nullptr;
+    if (S->e0) cudaEventDestroy(S->e0);
+    if (S->e1) cudaEventDestroy(S->e1);
     delete S;
     return EG_OK;
 }

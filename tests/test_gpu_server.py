@@ -76,7 +76,7 @@ def test_arrivals_from_threads_while_batches_run():
     gs = games()
     arenas = [eg.Arena(g) for g in gs]
     want = {i: alone(a.handle, 0, 1, 0, g.n) for i, (g, a) in enumerate(zip(gs, arenas))}
-    server = eg.eg_server_create(8 << 30, 4)  # small batches: later arrivals join later batches
+    server = eg.eg_server_create(8 << 30, 4)  # 4 slots: later arrivals wait for a free slot
     got, errors = [], []
 
     def client(seed):
@@ -138,3 +138,36 @@ def test_destroy_with_pending_requests():
         eg.eg_submit(server, a.handle, 0, 1, 0)
     eg.eg_server_destroy(server)  # returns after the running batch; queued ones are dropped
     a.close()
+
+
+def test_late_arrivals_join_the_running_solve():
+    # a slow game (a 64 x 64 grid without certified caps takes thousands of
+    # rounds) is being solved when small games arrive: they join the
+    # resident solve at its next round and finish while the slow one runs,
+    # and every result equals the solve of that game alone
+    slow = gen.grid_game(64, 64, seed=1)
+    smalls = [gen.config(1, s) for s in (2, 3, 4)] + [gen.rmat_game(10, 8, seed=5)]
+    a_slow = eg.Arena(slow)
+    a_small = [eg.Arena(g) for g in smalls]
+    server = eg.eg_server_create(2 << 30, 8)
+    try:
+        t_slow = eg.eg_submit(server, a_slow.handle, 64, 1, 0)
+        time.sleep(0.05)
+        ts = [eg.eg_submit(server, a.handle, 0, 1, 0) for a in a_small]
+        for g, a, t in zip(smalls, a_small, ts):
+            out = np.empty(g.n, dtype=np.int64)
+            rc, st = wait(server, t, out)
+            assert rc == eg.EG_OK, eg.eg_last_error()
+            np.testing.assert_array_equal(out, alone(a.handle, 0, 1, 0, g.n))
+        rc, _ = eg.eg_poll(server, t_slow)
+        assert rc == eg.EG_PENDING  # the small games did not wait for it
+        out = np.empty(slow.n, dtype=np.int64)
+        rc, st = wait(server, t_slow, out, timeout=120)
+        assert rc == eg.EG_OK
+        np.testing.assert_array_equal(out, alone(a_slow.handle, 64, 1, 0, slow.n))
+        assert st.rounds > 0 and st.fixpoint_ms > 0
+    finally:
+        eg.eg_server_destroy(server)
+        a_slow.close()
+        for a in a_small:
+            a.close()
