@@ -66,6 +66,7 @@ struct InstTable {
     const long long *shift;
     const long long *C;
     const int *inst_id;  // non-null: instance of each credit (resident solves)
+    const int *active;   // non-null: instances with active[i] == 0 are left as they are
 };
 
 template <typename T>
@@ -121,6 +122,13 @@ __device__ __forceinline__ View view_of(const Args<T> &a, int g) {
     if (!MULTI) return View{0, a.W.scale, a.W.shift, a.W.C};
     const int i = inst_of(a.I, g);
     return View{__ldg(a.I.delta + i), __ldg(a.I.scale + i), __ldg(a.I.shift + i), __ldg(a.I.C + i)};
+}
+
+// Whether credit g belongs to an instance this launch works on.
+template <bool MULTI, typename T>
+__device__ __forceinline__ bool in_active(const Args<T> &a, int g) {
+    if (!MULTI || !a.I.active) return true;
+    return __ldg(a.I.active + inst_of(a.I, g)) != 0;
 }
 
 // View of a lane that holds no entry.  It must still be the instance's view
@@ -183,6 +191,7 @@ __global__ void k_seed(Args<T> a, long long max_pairs, unsigned *seed_bits, unsi
     const int nw = gridDim.x * (blockDim.x >> 5);
     unsigned found_total = 0;
     for (int g = g0 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < g1; g += nw) {
+        if (!in_active<MULTI>(a, g)) continue;
         const View vw = view_of<MULTI>(a, g);
         const int u = g - vw.delta;
         if (!(((__ldg(A.owner_bits + (u >> 5)) >> (u & 31)) & 1u) ^ a.inv)) continue;
@@ -243,7 +252,7 @@ __global__ void __launch_bounds__(THREADS) k_init(Args<T> a, int g0, int g1, int
         const int g = base + threadIdx.x;
         bool want = false;
         int work = 0;
-        if (g < g1) {
+        if (g < g1 && in_active<MULTI>(a, g)) {
             const View vw = view_of<MULTI>(a, g);
             const int v = g - vw.delta;
             const bool p1 = ((__ldg(A.owner_bits + (v >> 5)) >> (v & 31)) & 1u) ^ a.inv;
@@ -1019,6 +1028,42 @@ __global__ void k_count_undecided(const T *f, const unsigned *w1, int n, unsigne
     }
 }
 
+// Per-instance count of credits at TOP that no proof puts in W1 (a warp
+// whose credits all belong to one instance adds them with one atomic).
+template <typename T>
+__global__ void k_count_undecided_inst(const T *f, const unsigned *w1, InstTable I, int nf,
+                                       unsigned long long *count) {
+    const int lane = lane_id();
+    for (int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < nf; base += gridDim.x * blockDim.x) {
+        const int g = base + lane;
+        int i = -1;
+        unsigned long long und = 0;
+        if (g < nf) {
+            i = inst_of(I, g);
+            und = f[g] == Cred<T>::TOP && !((w1[g >> 5] >> (g & 31)) & 1u);
+        }
+        const int i0 = __shfl_sync(FULL, i, 0);
+        if (__all_sync(FULL, i == i0)) {
+            for (int d = 16; d; d >>= 1) und += __shfl_down_sync(FULL, und, d);
+            if (lane == 0 && und) atomicAdd(count + i0, und);
+        } else if (und) {
+            atomicAdd(count + i, und);
+        }
+    }
+}
+
+// Marks the instance of every entry of the pull and push lists of round r
+// (list counter `slot`) of a batched solve.
+__global__ void k_busy_plan(const Ctrl *c, int slot, const int *pull_items, const int *push_items, InstTable I,
+                            int *busy) {
+    const int np = (int)(ld_cg(&c->pull_ctr[slot]) & 0xffffffffu);
+    const int nq = (int)(ld_cg(&c->push_ctr[slot]) & 0xffffffffu);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np + nq; i += gridDim.x * blockDim.x) {
+        const int g = (i < np ? ld_cg(pull_items + i) : ld_cg(push_items + (i - np))) & 0x7fffffff;
+        busy[inst_of(I, g)] = 1;
+    }
+}
+
 // Counters summed over the fixpoint launches of one solve.
 struct Totals {
     long long rounds = 0, lifts = 0, pushes = 0, relax = 0, enqueues = 0, seeded = 0;
@@ -1266,6 +1311,14 @@ struct eg_plan_impl {
     int graph_opts[3] = {-1, -1, -1};
     long long graph_pairs = -1;
     bool graph_failed = false;
+    // certified trial caps (allocated on first use)
+    std::vector<long long> wmax;  // max |w'| per instance
+    void *cert_block = nullptr;
+    long long *d_s2 = nullptr, *d_h2 = nullptr, *d_C2 = nullptr;
+    int *d_active = nullptr, *d_busy = nullptr;
+    unsigned long long *d_cnt = nullptr;
+    unsigned *cert_w0 = nullptr, *cert_w1 = nullptr;
+    StateBuffers sd;  // int64 state of the dual lifts
 };
 
 eg_status plan_release(eg_plan_impl *p);
@@ -1275,6 +1328,8 @@ eg_status plan_release(eg_plan_impl *p) {
     if (!p) return EG_OK;
     if (p->graph) cudaGraphExecDestroy(p->graph);
     free_state(p->sb);
+    free_state(p->sd);
+    if (p->cert_block) cudaFree(p->cert_block);
     if (p->table) cudaFree(p->table);
     if (p->own) cudaStreamDestroy(p->own);
     if (p->ev0) cudaEventDestroy(p->ev0);
@@ -1383,10 +1438,12 @@ eg_status plan_create(eg_arena *ar, int count, const int32_t *part, const int64_
     PTRY(cudaMemcpyAsync(hc.data(), d_accC, (size_t)2 * count * 8, cudaMemcpyDeviceToHost, s));
     PTRY(cudaStreamSynchronize(s));
     p->C.resize(count);
+    p->wmax.resize(count);
     p->bits_alone.resize(count);
     bool all32 = true;
     for (int i = 0; i < count; ++i) {
         p->C[i] = (long long)hc[i];
+        p->wmax[i] = (long long)hc[count + i];
         const bool fits = (long long)hc[i] + (long long)hc[count + i] <= 0x7fffffffLL - 1;
         p->bits_alone[i] = fits ? 32 : 64;
         all32 = all32 && fits;
@@ -1428,9 +1485,212 @@ void plan_instance_info(const eg_plan_impl *p, int i, long long *offset, long lo
     if (bits) *bits = p->bits_alone[i];
 }
 
+static void plan_add_totals(Totals &t, const eg_plan_impl *p, bool kernel_event) {
+    const Ctrl *hc = (const Ctrl *)p->host_ctrl;
+    float ms = 0.f, kms = 0.f;
+    cudaEventElapsedTime(&ms, p->ev0, p->ev1);
+    if (kernel_event) cudaEventElapsedTime(&kms, p->evk, p->ev1);
+    t.rounds += (long long)hc->rounds;
+    t.lifts += (long long)hc->lifts;
+    t.pushes += (long long)hc->pushes;
+    t.relax += (long long)hc->relax;
+    t.enqueues += (long long)hc->enqueues;
+    t.seeded = (long long)hc->seeded;
+    t.ms += ms;
+    t.kms += kernel_event ? kms : ms;
+}
+
+// One batched solve over the instances of I (direct launches), run to its end.
+template <typename T>
+static eg_status plan_phase(eg_plan_impl *p, StateBuffers &sb, const InstTable &I, const Launch &L, cudaStream_t s,
+                            Totals &t, int &dev) {
+    EG_CUDA_TRY(cudaEventRecord(p->ev0, s));
+    eg_status rc = enqueue_solve<true, T>(p->ar->d, WeightView{1, 0, 0}, I, p->nf, sb, L, p->ar->device, s, p->evk);
+    if (rc != EG_OK) return rc;
+    EG_CUDA_TRY(cudaEventRecord(p->ev1, s));
+    EG_CUDA_TRY(cudaMemcpyAsync(p->host_ctrl, sb.d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    EG_CUDA_TRY(cudaStreamSynchronize(s));
+    plan_add_totals(t, p, true);
+    dev = ((const Ctrl *)p->host_ctrl)->status;
+    if (dev != DEV_OK) sb.dirty = true;
+    return EG_OK;
+}
+
+// Certified trial caps per instance (readings of the single solve's trials):
+// instances the budgeted first attempt finished are exact; every other one
+// runs dual and capped lifts with its own B and K until it is decided, and
+// is then left as it is by the later launches.  What no trial decides ends
+// with cap C from its proven TOP starts.
+template <typename T>
+static eg_status plan_certify(eg_plan_impl *p, cudaStream_t s, long long max_rounds, Totals &t, int &dev) {
+    eg_arena *ar = p->ar;
+    const int cnt = p->count;
+    const long long nf = p->nf;
+    const size_t words = ((size_t)nf + 31) / 32, bm = align_up(words * 4);
+    if (!p->cert_block) {
+        const size_t o_h2 = align_up((size_t)cnt * 8), o_C2 = o_h2 + align_up((size_t)cnt * 8);
+        const size_t o_act = o_C2 + align_up((size_t)cnt * 8), o_busy = o_act + align_up((size_t)cnt * 4);
+        const size_t o_cnt = o_busy + align_up((size_t)cnt * 4), o_w0 = o_cnt + align_up((size_t)cnt * 8);
+        const size_t bytes = o_w0 + 2 * bm;
+        char *b = nullptr;
+        EG_CUDA_TRY(cudaMalloc((void **)&b, bytes));
+        p->cert_block = b;
+        p->d_s2 = (long long *)b;
+        p->d_h2 = (long long *)(b + o_h2);
+        p->d_C2 = (long long *)(b + o_C2);
+        p->d_active = (int *)(b + o_act);
+        p->d_busy = (int *)(b + o_busy);
+        p->d_cnt = (unsigned long long *)(b + o_cnt);
+        p->cert_w0 = (unsigned *)(b + o_w0);
+        p->cert_w1 = (unsigned *)(b + o_w0 + bm);
+    }
+    // instances with no entry left in the lists are finished, hence exact
+    const int r = (int)((const Ctrl *)p->host_ctrl)->r_next;
+    EG_CUDA_TRY(cudaMemsetAsync(p->d_busy, 0, (size_t)cnt * 4, s));
+    const int sms = num_sms(ar->device);
+    k_busy_plan<<<sms * 4, 256, 0, s>>>(p->sb.d.ctrl, r % 3, p->sb.d.pull_items[r & 1], p->sb.d.push_items[r & 1],
+                                        p->I, p->d_busy);
+    EG_CUDA_TRY(cudaGetLastError());
+    std::vector<int> act(cnt, 0);
+    EG_CUDA_TRY(cudaMemcpyAsync(act.data(), p->d_busy, (size_t)cnt * 4, cudaMemcpyDeviceToHost, s));
+    EG_CUDA_TRY(cudaStreamSynchronize(s));
+    p->sb.dirty = true;
+    int nact = 0;
+    for (int i = 0; i < cnt; ++i) nact += act[i] != 0;
+    if (nact == 0) return EG_OK;
+    if (p->sd.bits != 64 || p->sd.nf != nf) {
+        eg_status rc = alloc_state(p->sd, nf, 64);
+        if (rc != EG_OK) return rc;
+    }
+    EG_CUDA_TRY(cudaMemsetAsync(p->cert_w0, 0, 2 * bm, s));
+    constexpr long long LIM = 1LL << 61;
+    const long long raw = std::max(1LL, ar->wmax_plain), mult = ar->cap_certify;
+    std::vector<long long> B(cnt, 0), K(cnt, 0), hs(cnt), hh(cnt), hC(cnt);
+    std::vector<int> direct(cnt, 0), skip(cnt, 0), on(cnt, 0);
+    std::vector<unsigned long long> und(cnt);
+    auto fits = [&](int i) {
+        const long long inner = (p->scale[i] < 0 ? -p->scale[i] : p->scale[i]) * raw +
+                                (p->shift[i] < 0 ? -p->shift[i] : p->shift[i]) + 1;
+        return K[i] <= LIM / inner && B[i] <= LIM / (K[i] + 1);
+    };
+    for (int i = 0; i < cnt; ++i) {
+        if (!act[i]) continue;
+        const long long wm = std::max(1LL, p->wmax[i]);
+        if (wm > LIM / 4 / mult) {
+            skip[i] = 1;
+            continue;
+        }
+        B[i] = mult * wm;
+        K[i] = std::min(8LL, (long long)p->n_of[i] + 1);
+        if (B[i] >= p->C[i]) direct[i] = 1;  // cap C: the capped lift is the exact one
+        else if (!fits(i)) skip[i] = 1;
+    }
+    InstTable It = p->I;
+    It.scale = p->d_s2;
+    It.shift = p->d_h2;
+    It.C = p->d_C2;
+    It.active = p->d_active;
+    auto upload = [&](const std::vector<int> &a) -> eg_status {
+        EG_CUDA_TRY(cudaMemcpyAsync(p->d_s2, hs.data(), (size_t)cnt * 8, cudaMemcpyHostToDevice, s));
+        EG_CUDA_TRY(cudaMemcpyAsync(p->d_h2, hh.data(), (size_t)cnt * 8, cudaMemcpyHostToDevice, s));
+        EG_CUDA_TRY(cudaMemcpyAsync(p->d_C2, hC.data(), (size_t)cnt * 8, cudaMemcpyHostToDevice, s));
+        EG_CUDA_TRY(cudaMemcpyAsync(p->d_active, a.data(), (size_t)cnt * 4, cudaMemcpyHostToDevice, s));
+        EG_CUDA_TRY(cudaStreamSynchronize(s));  // the host vectors change before the next upload
+        return EG_OK;
+    };
+    const int wblocks = (int)std::min<long long>((nf + 255) / 256, (long long)sms * 16);
+    eg_status rc = EG_OK;
+    for (int k = 0; k < CERT_TRIALS; ++k) {
+        int ntrial = 0, ndual = 0;
+        for (int i = 0; i < cnt; ++i) {
+            on[i] = act[i] && !skip[i];
+            ntrial += on[i];
+        }
+        if (ntrial == 0) break;
+        // dual lifts: owners swapped, weights -(K w' + 1), cap (K + 1) B
+        std::vector<int> dual_on(cnt, 0);
+        for (int i = 0; i < cnt; ++i) {
+            hs[i] = p->scale[i];
+            hh[i] = p->shift[i];
+            hC[i] = p->C[i];
+            if (on[i] && !direct[i]) {
+                dual_on[i] = 1;
+                ++ndual;
+                hs[i] = -K[i] * p->scale[i];
+                hh[i] = 1 - K[i] * p->shift[i];
+                hC[i] = (K[i] + 1) * B[i];
+            }
+        }
+        if (ndual > 0) {
+            if ((rc = upload(dual_on)) != EG_OK) return rc;
+            EG_CUDA_TRY(cudaMemcpyAsync(p->sd.d.seed_bits, p->cert_w0, words * 4, cudaMemcpyDeviceToDevice, s));
+            Launch Ld{ar->local_windows, ar->local_maxdeg, 1, ar->seed_max_pairs, max_rounds};
+            Ld.inv = 1;
+            Ld.preseeded = true;
+            rc = plan_phase<long long>(p, p->sd, It, Ld, s, t, dev);
+            if (rc != EG_OK || dev != DEV_OK) return rc;
+            k_mark_finite<long long><<<wblocks, 256, 0, s>>>((const long long *)p->sd.d.f, (int)nf, p->cert_w1);
+            EG_CUDA_TRY(cudaGetLastError());
+        }
+        // the game's lifts with cap B (cap C for the direct ones)
+        for (int i = 0; i < cnt; ++i) {
+            hs[i] = p->scale[i];
+            hh[i] = p->shift[i];
+            hC[i] = on[i] && !direct[i] ? B[i] : p->C[i];
+        }
+        if ((rc = upload(on)) != EG_OK) return rc;
+        EG_CUDA_TRY(cudaMemcpyAsync(p->sb.d.seed_bits, p->cert_w1, words * 4, cudaMemcpyDeviceToDevice, s));
+        Launch Lp{ar->local_windows, ar->local_maxdeg, 1, ar->seed_max_pairs, max_rounds};
+        Lp.preseeded = true;
+        rc = plan_phase<T>(p, p->sb, It, Lp, s, t, dev);
+        if (rc != EG_OK || dev != DEV_OK) return rc;
+        EG_CUDA_TRY(cudaMemsetAsync(p->d_cnt, 0, (size_t)cnt * 8, s));
+        k_count_undecided_inst<T><<<wblocks, 256, 0, s>>>((const T *)p->sb.d.f, p->sb.d.seed_bits, It, (int)nf,
+                                                         p->d_cnt);
+        k_mark_finite<T><<<wblocks, 256, 0, s>>>((const T *)p->sb.d.f, (int)nf, p->cert_w0);
+        EG_CUDA_TRY(cudaGetLastError());
+        EG_CUDA_TRY(cudaMemcpyAsync(und.data(), p->d_cnt, (size_t)cnt * 8, cudaMemcpyDeviceToHost, s));
+        EG_CUDA_TRY(cudaStreamSynchronize(s));
+        for (int i = 0; i < cnt; ++i) {
+            if (!on[i]) continue;
+            if (direct[i] || und[i] == 0) {
+                act[i] = 0;  // exact: later launches leave it as it is
+                continue;
+            }
+            if (B[i] > LIM / 4) {
+                skip[i] = 1;
+                continue;
+            }
+            B[i] *= 4;
+            K[i] = std::min(K[i] * 8, (long long)p->n_of[i] + 1);
+            if (B[i] >= p->C[i]) direct[i] = 1;
+            else if (!fits(i)) skip[i] = 1;
+        }
+    }
+    int left = 0;
+    for (int i = 0; i < cnt; ++i) left += act[i] != 0;
+    if (left == 0) return EG_OK;
+    // cap C from the proven TOP starts for whatever no trial decided
+    for (int i = 0; i < cnt; ++i) {
+        hs[i] = p->scale[i];
+        hh[i] = p->shift[i];
+        hC[i] = p->C[i];
+    }
+    if ((rc = upload(act)) != EG_OK) return rc;
+    EG_CUDA_TRY(cudaMemcpyAsync(p->sb.d.seed_bits, p->cert_w1, words * 4, cudaMemcpyDeviceToDevice, s));
+    Launch Lf{ar->local_windows, ar->local_maxdeg, 1, ar->seed_max_pairs, max_rounds};
+    Lf.preseeded = true;
+    return plan_phase<T>(p, p->sb, It, Lf, s, t, dev);
+}
+
 eg_status plan_run(eg_plan_impl *p, void *out, eg_stats *st, cudaStream_t user, long long max_rounds) {
     eg_arena *ar = p->ar;
-    const Launch L{ar->local_windows, ar->local_maxdeg, ar->warm_start, ar->seed_max_pairs, max_rounds};
+    // with certification on, the first batched solve gets a short round
+    // budget, and only the instances it does not finish go through the trials
+    const bool cert = ar->cap_certify > 0 && ar->warm_start && ar->certify_after > 0 &&
+                      (max_rounds == 0 || max_rounds > ar->certify_after);
+    const Launch L{ar->local_windows, ar->local_maxdeg, ar->warm_start, ar->seed_max_pairs,
+                   cert ? ar->certify_after : max_rounds};
     cudaStream_t s = user ? user : p->own;
     // scratch left dirty by an aborted run is reset outside the graph
     if (p->sb.dirty) {
@@ -1444,7 +1704,7 @@ eg_status plan_run(eg_plan_impl *p, void *out, eg_stats *st, cudaStream_t user, 
         }
         p->sb.dirty = false;
     }
-    const bool same = p->graph && p->graph_rounds == max_rounds && p->graph_opts[0] == L.local_windows &&
+    const bool same = p->graph && p->graph_rounds == L.max_rounds && p->graph_opts[0] == L.local_windows &&
                       p->graph_opts[1] == L.local_maxdeg && p->graph_opts[2] == L.warm_start &&
                       p->graph_pairs == L.seed_max_pairs;
     if (!ar->use_graph && p->graph) {
@@ -1466,7 +1726,7 @@ eg_status plan_run(eg_plan_impl *p, void *out, eg_stats *st, cudaStream_t user, 
         if (g) cudaGraphDestroy(g);
         cudaGetLastError();
         if (ok) {
-            p->graph_rounds = max_rounds;
+            p->graph_rounds = L.max_rounds;
             p->graph_opts[0] = L.local_windows;
             p->graph_opts[1] = L.local_maxdeg;
             p->graph_opts[2] = L.warm_start;
@@ -1484,6 +1744,18 @@ eg_status plan_run(eg_plan_impl *p, void *out, eg_stats *st, cudaStream_t user, 
         if (rc != EG_OK) return rc;
     }
     EG_CUDA_TRY(cudaEventRecord(p->ev1, s));
+    Totals tot;
+    int dev = DEV_OK;
+    if (cert) {
+        EG_CUDA_TRY(cudaStreamSynchronize(s));
+        plan_add_totals(tot, p, p->graph == nullptr);
+        dev = ((const Ctrl *)p->host_ctrl)->status;
+        if (dev == DEV_BUDGET) {
+            eg_status rc = p->bits == 32 ? plan_certify<int>(p, s, max_rounds, tot, dev)
+                                         : plan_certify<long long>(p, s, max_rounds, tot, dev);
+            if (rc != EG_OK) return rc;
+        }
+    }
     // credits out
     cudaPointerAttributes attr{};
     const bool dev_out = cudaPointerGetAttributes(&attr, out) == cudaSuccess &&
@@ -1501,15 +1773,16 @@ eg_status plan_run(eg_plan_impl *p, void *out, eg_stats *st, cudaStream_t user, 
                                 dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
     if (tmp) EG_CUDA_TRY(cudaFreeAsync(tmp, s));
     EG_CUDA_TRY(cudaStreamSynchronize(s));
-    const Ctrl *hc = (const Ctrl *)p->host_ctrl;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, p->ev0, p->ev1);
+    if (!cert) {
+        plan_add_totals(tot, p, p->graph == nullptr);
+        dev = ((const Ctrl *)p->host_ctrl)->status;
+    }
     eg_status result = EG_OK;
-    if (hc->status == DEV_TIMEOUT) {
+    if (dev == DEV_TIMEOUT) {
         set_error("a device-side wait exceeded its limit");
         result = EG_ERR_TIMEOUT;
         p->sb.dirty = true;
-    } else if (hc->status == DEV_BUDGET) {
+    } else if (dev == DEV_BUDGET) {
         set_error("round budget of %lld exhausted", max_rounds);
         result = EG_ERR_BUDGET;
         p->sb.dirty = true;
@@ -1518,16 +1791,16 @@ eg_status plan_run(eg_plan_impl *p, void *out, eg_stats *st, cudaStream_t user, 
         long long cmax = 0;
         for (long long c : p->C) cmax = std::max(cmax, c);
         st->C = cmax;
-        st->seeded = (int64_t)hc->seeded;
+        st->seeded = (int64_t)tot.seeded;
         st->credit_bits = p->bits;
         st->status = result;
-        st->rounds = (int64_t)hc->rounds;
-        st->lifts = (int64_t)hc->lifts;
-        st->pushes = (int64_t)hc->pushes;
-        st->relaxations = (int64_t)hc->relax;
-        st->enqueues = (int64_t)hc->enqueues;
-        st->ms = ms;
-        st->fixpoint_ms = p->graph ? -1.0 : ms;
+        st->rounds = (int64_t)tot.rounds;
+        st->lifts = (int64_t)tot.lifts;
+        st->pushes = (int64_t)tot.pushes;
+        st->relaxations = (int64_t)tot.relax;
+        st->enqueues = (int64_t)tot.enqueues;
+        st->ms = tot.ms;
+        st->fixpoint_ms = p->graph ? -1.0 : tot.kms;
     }
     return result;
 }

@@ -146,3 +146,41 @@ def test_batch_round_budget_then_run():
                 np.testing.assert_array_equal(out[off:off + n], ref(g))
     finally:
         eg.eg_destroy(h)
+
+
+@pytest.mark.parametrize("after", [64, 0, 3])
+@pytest.mark.parametrize("mult", [4, 1])
+def test_batch_certified_trials_per_instance(after, mult):
+    # grids need the certified trials; the small games finish in the first
+    # attempt (after > 0) and must stay as they are through the later trials
+    games = [gen.grid_game(40, 40, seed=3), gen.grid_game(24, 50, seed=8), gen.config(1, 5),
+             gen.rmat_game(10, 8, seed=9), gen.varied_game(2500, 2, 16, 5000, seed=12),
+             gen.tiny_game(7, 3, -3, 3, seed=4)]
+    h = packed_arena(games)
+    try:
+        eg.eg_set_option(h, eg.EG_OPT_CAP_CERTIFY, mult)
+        eg.eg_set_option(h, eg.EG_OPT_CERTIFY_AFTER, after)
+        with eg.Plan(h, len(games)) as plan:
+            out, st = plan.run()
+            for k, g in enumerate(games):
+                off, n, _, _ = plan.instance(k)
+                np.testing.assert_array_equal(out[off:off + n], ref(g))
+            again, _ = plan.run()
+            np.testing.assert_array_equal(again, out)
+    finally:
+        eg.eg_destroy(h)
+
+
+def test_threshold_batch_certified_against_oracle():
+    a = gen.rmat_game(12, 8, seed=21)
+    ks = [-100, -20, -3, -1, 0, 1, 2, 5, 40, 127]
+    W = 100
+    h = eg.eg_create(a.n, a.m, a.row_ptr, a.col, a.w, owner_bits=a.owner_bits)
+    try:
+        with eg.Plan(h, len(ks), part=[0] * len(ks), w_scale=[256] * len(ks), w_shift=[k * W for k in ks]) as plan:
+            out, _ = plan.run()
+            for i, k in enumerate(ks):
+                off, n, _, _ = plan.instance(i)
+                np.testing.assert_array_equal(out[off:off + n], ref(a, gen.threshold_weights(a.w, k, W)))
+    finally:
+        eg.eg_destroy(h)

@@ -189,3 +189,46 @@ def test_pins_pass_on_real_oracle():
 def test_pins_catch_planted_mistake(name):
     with tempfile.TemporaryDirectory() as d:
         assert not _pins_pass(_mutant_lib(d, name)), f"mutant {name} slipped through the pins"
+
+
+# ---- the facts certified trial caps rest on, checked by brute force --------
+# (1) In the dual game -- weights -(K w + 1), owners swapped -- a vertex with a
+#     finite least-EPM value under any cap is won by player 1 in the game.
+# (2) If, for a cap B, every vertex is finite in the game's capped least
+#     fixpoint or proven lost by (1), that capped fixpoint is the least EPM.
+
+def _dual(a, K):
+    w2 = -(np.int64(K) * np.asarray(a.w, dtype=np.int64)) - 1
+    ob2 = (~np.asarray(a.owner_bits, dtype=np.uint32)).astype(np.uint32)
+    return w2, ob2
+
+
+@pytest.mark.parametrize("block", range(10))
+def test_dual_finite_only_on_player1_wins(block):
+    for seed in range(block * 60, block * 60 + 60):
+        a = _tiny(seed)
+        exact = oracle.brute_force(a.n, a.row_ptr, a.col, a.w, a.owner_bits)
+        maxw = int(np.abs(a.w).max()) if a.w.size else 0
+        for K in (1, 2, 8, a.n + 1):
+            w2, ob2 = _dual(a, K)
+            for B in (1, maxw, 4 * maxw + 3):
+                g, _ = oracle.solve(a.n, a.row_ptr, a.col, w2, ob2, C=(K + 1) * B)
+                fin = g != TOP64
+                assert (exact[fin] == TOP64).all(), (seed, K, B)
+
+
+@pytest.mark.parametrize("block", range(10))
+def test_capped_fixpoint_exact_when_every_vertex_is_decided(block):
+    decided_runs = 0
+    for seed in range(block * 60, block * 60 + 60):
+        a = _tiny(seed)
+        exact = oracle.brute_force(a.n, a.row_ptr, a.col, a.w, a.owner_bits)
+        maxw = max(1, int(np.abs(a.w).max()) if a.w.size else 1)
+        w2, ob2 = _dual(a, 8)
+        for B in (maxw, 2 * maxw, 4 * maxw):
+            proven = oracle.solve(a.n, a.row_ptr, a.col, w2, ob2, C=9 * B)[0] != TOP64
+            f, _ = oracle.solve(a.n, a.row_ptr, a.col, a.w, a.owner_bits, C=B)
+            if ((f != TOP64) | proven).all():
+                decided_runs += 1
+                np.testing.assert_array_equal(f, exact)
+    assert decided_runs > 0
