@@ -46,6 +46,17 @@ def algorithmic_bytes(st, s):
     return st["relaxations"] * (8 + s) + (st["lifts"] + st["pushes"]) * (12 + s) + st["enqueues"] * 8
 
 
+def kernel_source_hash():
+    """SHA-256 over the sources the fixpoint kernel is compiled from."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for name in ("eg_solve.cu", "eg_device.cuh", "eg_internal.h"):
+        with open(os.path.join(ROOT, "paper_1710_03647_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -55,7 +66,9 @@ def peaks():
 
 
 class ClockSampler:
-    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+    """Samples nvidia-smi clocks and throttle reasons every 20 ms from before
+    the warm-up to the end of the timed region; each sample is stamped with
+    the host time it arrived, and mark() brackets the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -66,11 +79,12 @@ class ClockSampler:
         self.rows = []
         self.proc = None
         self.thread = None
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -80,10 +94,17 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
+            self.rows.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def mark(self, begin):
+        if begin:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
 
     def __exit__(self, *exc):
         if self.proc:
+            time.sleep(0.05)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -91,14 +112,19 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        if not self.rows:
+        inside = [r for t, r in self.rows if self.t0 is not None and self.t0 <= t <= (self.t1 or t) + 0.03]
+        window = "timed"
+        rows = inside
+        if not rows:
+            rows, window = [r for _, r in self.rows], "warm-up and timed"
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
+        reasons = sorted({names[i] for r in rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(rows), "window": window}
 
 
 def reduce_over_ranks(total_ms, relax, device, dist):
@@ -384,15 +410,16 @@ def main():
         _, st = eg.eg_solve_credit(arena.handle, bits, 1, 0, out, stream=stream.cuda_stream)
         return st
 
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     stats = []
-    if pg:
-        pg.barrier()
-    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        for _ in range(max(args.warmup, 3)):
+            step()
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        clk.mark(True)
         for k in range(args.steps):
             with torch.cuda.stream(stream):
                 flush.fill_(k & 0xff)  # rewrite > L2 between steps (untimed)
@@ -401,6 +428,7 @@ def main():
             ev[k][1].record(stream)
             stats.append(st.as_dict())
         torch.cuda.synchronize()
+        clk.mark(False)
     if pg:
         pg.barrier()
     step_ms = [b.elapsed_time(e) for b, e in ev]
@@ -421,7 +449,10 @@ def main():
     traffic = None
     prof = os.path.join(ROOT, "profiles", "fixpoint_rmat20_traffic.json")
     if os.path.exists(prof):
-        traffic = json.load(open(prof)).get("dram_bytes_per_launch")
+        rec = json.load(open(prof))
+        # counters taken on another version of the kernel say nothing about this one
+        if rec.get("kernel_source_sha256") == kernel_source_hash():
+            traffic = rec.get("dram_bytes_per_launch")
 
     # end to end through the public API: host arrays in, host credits out
     e2e = None

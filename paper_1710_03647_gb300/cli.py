@@ -1,0 +1,53 @@
+"""Command-line solve of a generated workload through the C ABI.
+
+    python -m paper_1710_03647_gb300.cli --workload grid --side 2000 --bits 64 \
+        --local-windows 0 --max-rounds 30 --repeat 3
+
+Builds the arena with the seeded generators of `gen`, applies the given
+solver options and prints the counters of every solve as one JSON line.  A
+round budget that runs out is reported, not raised (status -7).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+
+from paper_1710_03647_gb300 import eg, gen
+
+
+def main(argv=None) -> None:
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--workload", choices=["uniform", "rmat", "grid", "varied"], default="rmat")
+    ap.add_argument("--scale", type=int, default=20, help="R-MAT scale (2^scale vertices)")
+    ap.add_argument("--side", type=int, default=4000, help="grid side")
+    ap.add_argument("--n", type=int, default=100000, help="vertices of uniform / varied games")
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--bits", type=int, default=0, choices=[0, 32, 64])
+    ap.add_argument("--max-rounds", type=int, default=0)
+    ap.add_argument("--repeat", type=int, default=1)
+    for opt in ("local-windows", "local-maxdeg", "warm-start", "cap-certify", "certify-after"):
+        ap.add_argument("--" + opt, type=int, default=None)
+    args = ap.parse_args(argv)
+    if args.workload == "rmat":
+        a = gen.rmat_game(args.scale, 8, seed=args.seed)
+    elif args.workload == "grid":
+        a = gen.grid_game(args.side, args.side, seed=args.seed)
+    elif args.workload == "uniform":
+        a = gen.uniform_game(args.n, 4, -10, 10, seed=args.seed)
+    else:
+        a = gen.varied_game(args.n, 2, 16, 1000, seed=args.seed)
+    with eg.Arena(a) as arena:
+        arena.tune(local_windows=args.local_windows, local_maxdeg=args.local_maxdeg, warm_start=args.warm_start,
+                   cap_certify=args.cap_certify, certify_after=args.certify_after)
+        out = np.empty(a.n, dtype=np.int32 if args.bits == 32 else np.int64)
+        for _ in range(args.repeat):
+            rc, st = eg.eg_solve_credit(arena.handle, args.bits, 1, 0, out, max_rounds=args.max_rounds,
+                                        raise_on_error=False)
+            print(json.dumps({"workload": args.workload, "n": a.n, "m": a.m, "status": rc, **st.as_dict()}),
+                  flush=True)
+
+
+if __name__ == "__main__":
+    main()
