@@ -131,6 +131,26 @@ eg_status eg_solve_credit(eg_arena *arena, int32_t credit_bits, int64_t w_scale,
                           void *credits_out, eg_stats *st, void *cuda_stream, int64_t max_rounds);
 
 /*
+ * eg_strategy -- a winning positional strategy of player 0 read off the
+ * least EPM (Def. "EPM", Sec. 3.1; the problem statement of Sec. 3 asks for
+ * the credits and the strategies that achieve them).  For every player-0
+ * vertex v with a finite credit, succ_out[v] is the successor u of v's first
+ * out-edge (in CSR order) with f(u) (-) w'(v, u) = f(v); every other vertex
+ * gets -1.  Following it from v, player 0 never needs more than f(v)
+ * energy: every cycle of chosen edges has weight >= 0.
+ *
+ * credits: n credits of credit_bits (32 or 64), as eg_solve_credit wrote
+ * them for the same weight map w' = w_scale * w - w_shift; host or device
+ * pointer.  succ_out: int32[n], host or device pointer, caller-owned.
+ * Synchronous.  EG_ERR_INVALID if a finite player-0 credit is attained by
+ * no out-edge (then the credits are not the least EPM of this arena and
+ * map).  Allocates scratch of about n * (credit_bits / 8 + 4) bytes on the
+ * stream's memory pool.
+ */
+eg_status eg_strategy(eg_arena *arena, int32_t credit_bits, int64_t w_scale, int64_t w_shift, const void *credits,
+                      int32_t *succ_out, void *cuda_stream);
+
+/*
  * eg_set_option -- per-arena settings of later solves.  None of them changes
  * a result: they change only how fast the least fixpoint is reached.
  *

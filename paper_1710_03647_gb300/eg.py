@@ -69,6 +69,7 @@ SIGNATURES = {
     "eg_plan_run": (_I32, [_P, _P, ctypes.POINTER(eg_stats), _P, _I64]),
     "eg_plan_destroy": (_I32, [_P]),
     "eg_solve_credit_noalloc": (_I32, [_P, _I32, _I64, _I64, _P, ctypes.POINTER(eg_stats), _P, _I64]),
+    "eg_strategy": (_I32, [_P, _I32, _I64, _I64, _P, _P, _P]),
     "eg_server_create": (_I32, [ctypes.c_size_t, _I32, ctypes.POINTER(_P)]),
     "eg_submit": (_I32, [_P, _P, _I32, _I64, _I64, ctypes.POINTER(ctypes.c_uint64)]),
     "eg_poll": (_I32, [_P, ctypes.c_uint64, _P, ctypes.POINTER(eg_stats)]),
@@ -163,6 +164,28 @@ def eg_solve_credit_noalloc(arena, credit_bits, w_scale, w_shift, credits_out, s
     if raise_on_error:
         _check(rc)
     return rc, st
+
+
+def eg_strategy(arena, credit_bits, w_scale, w_shift, credits, succ_out=None, stream=None):
+    """Player 0's winning successor per vertex (-1 where none) from least-EPM
+    credits (numpy array or device tensor/address of credit_bits).  Returns
+    succ_out (a new int32 numpy array if None)."""
+    if isinstance(credits, np.ndarray):
+        want = np.int32 if credit_bits == 32 else np.int64
+        if credits.dtype != want or not credits.flags.c_contiguous:
+            raise TypeError(f"credits must be a contiguous {np.dtype(want)} array")
+        cptr = credits.ctypes.data
+        n = credits.shape[0]
+    else:
+        cptr = _addr(credits, None)
+        n = None
+    if succ_out is None:
+        if n is None:
+            raise ValueError("succ_out is required with device credits")
+        succ_out = np.empty(n, dtype=np.int32)
+    optr = succ_out.ctypes.data if isinstance(succ_out, np.ndarray) else _addr(succ_out, None)
+    _check(load().eg_strategy(arena, credit_bits, w_scale, w_shift, cptr, optr, stream))
+    return succ_out
 
 
 def eg_set_option(arena, option: int, value: int) -> None:

@@ -374,3 +374,77 @@ def test_road_grid_full_size_fixpoint():
     ntop = int((out == TOP64).sum())
     assert 0 < ntop < a.n
     assert st.seeded == ntop
+
+
+def _ominus(a, b, C):
+    if a == TOP64:
+        return TOP64
+    d = int(a) - int(b)
+    return TOP64 if d > C else max(0, d)
+
+
+@pytest.mark.parametrize("make,scale,shift", [
+    (lambda: gen.config(1, 3), 1, 0), (lambda: gen.rmat_game(12, 8, seed=2), 1, 0),
+    (lambda: gen.grid_game(32, 32, seed=6), 1, 0), (lambda: gen.varied_game(2000, 2, 16, 500, seed=5), 1, 0),
+    (lambda: gen.rmat_game(11, 8, seed=8), 256, -300), (lambda: gen.tiny_game(300, 4, -6, 6, seed=3), 1, 0)],
+    ids=["uniform1k", "rmat12", "grid32", "varied2k", "rmat11_threshold", "tiny300"])
+def test_strategy_attains_the_credits(make, scale, shift):
+    # restricting every winning player-0 vertex to its chosen edge must leave
+    # every credit unchanged (the oracle solves the restricted game)
+    a = make()
+    w = np.asarray(a.w, dtype=np.int64) * scale - shift
+    f = ref(a, w)
+    with eg.Arena(a) as ar:
+        out, st = ar.solve(credit_bits=64, w_scale=scale, w_shift=shift)
+        np.testing.assert_array_equal(out, f)
+        succ = eg.eg_strategy(ar.handle, 64, scale, shift, out)
+        import torch
+        dev_f = torch.from_numpy(out).cuda()
+        dev_s = torch.empty(a.n, dtype=torch.int32, device="cuda")
+        eg.eg_strategy(ar.handle, 64, scale, shift, dev_f, dev_s)
+        np.testing.assert_array_equal(dev_s.cpu().numpy(), succ)
+    C = oracle.bound(a.n, a.row_ptr, w)
+    p1 = gen.unpack_owner(a.owner_bits, a.n).astype(bool)
+    rp = np.asarray(a.row_ptr, dtype=np.int64)
+    rows, ws = [], []
+    for v in range(a.n):
+        lo, hi = int(rp[v]), int(rp[v + 1])
+        if p1[v] or f[v] == TOP64:
+            assert succ[v] == -1
+            rows.append(list(a.col[lo:hi]))
+            ws.append(list(w[lo:hi]))
+            continue
+        pick = next(e for e in range(lo, hi) if _ominus(f[int(a.col[e])], w[e], C) == f[v])
+        assert succ[v] == a.col[pick]
+        rows.append([int(a.col[pick])])
+        ws.append([int(w[pick])])
+    rrp = np.zeros(a.n + 1, dtype=np.int64)
+    rrp[1:] = np.cumsum([len(r) for r in rows])
+    rcol = np.array([c for r in rows for c in r], dtype=np.int32)
+    rw = np.array([x for r in ws for x in r], dtype=np.int64)
+    g, _ = oracle.solve(a.n, rrp, rcol, rw, a.owner_bits)
+    np.testing.assert_array_equal(g, f)
+
+
+def test_strategy_rejects_credits_that_are_not_the_least_epm():
+    a = gen.config(1, 4)
+    with eg.Arena(a) as ar:
+        out, _ = ar.solve(credit_bits=64)
+        bad = out.copy()
+        p1 = gen.unpack_owner(a.owner_bits, a.n).astype(bool)
+        v = int(np.nonzero(~p1 & (out != TOP64))[0][0])
+        bad[v] += 12345
+        with pytest.raises(eg.EGError) as ei:
+            eg.eg_strategy(ar.handle, 64, 1, 0, bad)
+        assert ei.value.status == eg.EG_ERR_INVALID
+
+
+def test_cli_solves_and_reports(capsys):
+    from paper_1710_03647_gb300 import cli
+
+    cli.main(["--workload", "grid", "--side", "24", "--bits", "64", "--repeat", "2"])
+    lines = [json.loads(x) for x in capsys.readouterr().out.strip().splitlines()]
+    assert len(lines) == 2 and all(x["status"] == 0 and x["n"] == 576 for x in lines)
+    cli.main(["--workload", "rmat", "--scale", "10", "--local-windows", "0", "--max-rounds", "1"])
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["status"] in (0, eg.EG_ERR_BUDGET) and line["rounds"] <= 1
