@@ -382,6 +382,24 @@ def serving(eg, gen, torch, dev, stream, per_rate, scales=(10, 17), seed=11):
                                    "64 slots, 16 GiB pool"}
 
 
+def cpu_parallel_baseline():
+    """The paper's Algorithm 2 (OpenMP lifting sweeps from f = 0) on all host
+    cores, on the same bounded sample as cpu_baseline: context for the
+    paper's multi-core CPU column."""
+    import oracle
+    from paper_1710_03647_gb300 import gen
+
+    scale = 16
+    a = gen.rmat_game(scale, 8, seed=WORKLOAD["seed"])
+    t0 = time.perf_counter()
+    _, st = oracle.sweep(a.n, a.row_ptr, a.col, a.w, a.owner_bits, threads=os.cpu_count() or 1)
+    dt = time.perf_counter() - t0
+    return {"value": st["edge_evals"] / dt, "unit": UNIT, "cores": st["threads"],
+            "kind": "paper Algorithm 2 (parallel lifting sweeps)", "time_to_fixpoint_s": dt,
+            "sweeps": st["sweeps"],
+            "sample": f"R-MAT scale {scale} (n={a.n}, m={a.m}) from the same generator, f = 0 start, one full solve"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -565,6 +583,7 @@ def main():
         g = json.load(open(golden))
         oracle_relax = g["oracle_lift_edge_evals"] + g["oracle_pre_scans"]
     cpu = None if args.no_cpu_baseline else cpu_baseline()
+    cpu_par = None if args.no_cpu_baseline else cpu_parallel_baseline()
     st0 = stats[-1]
     line = {
         "metric": METRIC, "value": relax_all / (total_ms_max * 1e-3), "unit": UNIT, "n_gpus": world,
@@ -581,6 +600,7 @@ def main():
                      "algorithmic_bytes_per_launch": bytes_alg / args.steps,
                      "kernel_ms_per_launch": fix_ms / args.steps},
         "cpu_baseline": cpu,
+        "cpu_parallel_baseline": cpu_par,
         "warm_start_seeded": st0["seeded"],
         "plain": plain,
         "threshold_queries": thresholds,

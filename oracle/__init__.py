@@ -9,6 +9,11 @@ no code with the CUDA solver.  `oracle.c` holds the arithmetic:
   brute_force(...)  Lemma "EGcycles" by strategy enumeration + Bellman-Ford
   check(...)        least-EPM equations of Def. "EPM" / "Lifting Operator"
 
+`sweep.c` (its own library, built with OpenMP) is the paper's Algorithm 2,
+the multi-core CPU baseline the benchmark times as context:
+
+  sweep(...)        parallel in-place lifting sweeps from f = 0
+
 Credits are int64 numpy arrays with TOP = INT64_MAX.
 """
 from __future__ import annotations
@@ -24,16 +29,21 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIB_DIR, "liboracle.so")
+_SWEEP_SRC = os.path.join(_HERE, "sweep.c")
+_SWEEP_LIB = os.path.join(_LIB_DIR, "liboracle_sweep.so")
 _lib = None
+_sweep_lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into a shared library with the host C compiler."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        os.makedirs(_LIB_DIR, exist_ok=True)
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC])
-        os.replace(tmp, _LIB)
+    """Compile oracle.c (and sweep.c, with OpenMP) into shared libraries
+    with the host C compiler."""
+    for src, lib, extra in ((_SRC, _LIB, []), (_SWEEP_SRC, _SWEEP_LIB, ["-fopenmp"])):
+        if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+            os.makedirs(_LIB_DIR, exist_ok=True)
+            tmp = lib + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", *extra, "-o", tmp, src])
+            os.replace(tmp, lib)
     return _LIB
 
 
@@ -124,3 +134,31 @@ def check(n: int, row_ptr, col, w, owner_bits, f, C: int | None = None):
     rc = _load().oracle_check(n, _ptr(row_ptr), _ptr(col), _ptr(w), _ptr(owner_bits), C, _ptr(f),
                               _ptr(bad))
     return int(rc), int(bad[0])
+
+
+def _load_sweep():
+    global _sweep_lib
+    if _sweep_lib is None:
+        build()
+        lib = ctypes.CDLL(_SWEEP_LIB)
+        i64, p = ctypes.c_int64, ctypes.c_void_p
+        lib.oracle_sweep.restype = ctypes.c_int
+        lib.oracle_sweep.argtypes = [i64, p, p, p, p, i64, i64, ctypes.c_int, p, p]
+        _sweep_lib = lib
+    return _sweep_lib
+
+
+def sweep(n: int, row_ptr, col, w, owner_bits, C: int | None = None, max_sweeps: int = 0, threads: int = 0):
+    """Algorithm 2 (parallel sweeps).  Returns (f int64[n] with TOP, stats dict)."""
+    row_ptr, col, w, owner_bits = _arrays(row_ptr, col, w, owner_bits)
+    if C is None:
+        C = bound(n, row_ptr, w)
+    f = np.zeros(max(n, 1), dtype=np.int64)
+    st = np.zeros(3, dtype=np.int64)
+    rc = _load_sweep().oracle_sweep(n, _ptr(row_ptr), _ptr(col), _ptr(w), _ptr(owner_bits), C, max_sweeps,
+                                    threads, _ptr(f), _ptr(st))
+    if rc == 1:
+        raise OracleError("arena is not total: a vertex has no successor")
+    if rc == 2:
+        raise OracleError(f"sweep budget of {max_sweeps} exhausted")
+    return f[:n], dict(C=C, sweeps=int(st[0]), edge_evals=int(st[1]), threads=int(st[2]))

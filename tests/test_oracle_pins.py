@@ -232,3 +232,19 @@ def test_capped_fixpoint_exact_when_every_vertex_is_decided(block):
                 decided_runs += 1
                 np.testing.assert_array_equal(f, exact)
     assert decided_runs > 0
+
+
+# ---- the paper's Algorithm 2 (CPU baseline) reaches the same least fixpoint --
+
+@pytest.mark.parametrize("threads", [1, 4])
+def test_sweep_baseline_matches_algorithm_1(threads):
+    for a in [gen.config(1, 1), gen.config(1, 2), gen.rmat_game(10, 8, seed=3),
+              gen.varied_game(1500, 2, 16, 200, seed=4), gen.grid_game(12, 12, seed=2)]:
+        f, _ = solve(a)
+        g, st = oracle.sweep(a.n, a.row_ptr, a.col, a.w, a.owner_bits, threads=threads)
+        np.testing.assert_array_equal(g, f)
+        assert st["sweeps"] >= 1 and st["edge_evals"] == st["sweeps"] * a.m
+    for seed in range(300):
+        a = _tiny(seed)
+        g, _ = oracle.sweep(a.n, a.row_ptr, a.col, a.w, a.owner_bits, threads=threads)
+        np.testing.assert_array_equal(g, oracle.brute_force(a.n, a.row_ptr, a.col, a.w, a.owner_bits))
