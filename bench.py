@@ -410,7 +410,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the context solve without warm start")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched threshold-query comparison")
     ap.add_argument("--no-large", action="store_true", help="skip the 4000x4000 grid solve")
-    ap.add_argument("--batch-games", type=int, default=512, help="games in the batched-vs-per-game comparison "
+    ap.add_argument("--batch-games", type=int, default=4096, help="games in the batched-vs-per-game comparison "
                     "(4096 = the full workload; 0 skips it)")
     ap.add_argument("--serve-requests", type=int, default=96, help="requests per arrival rate (0 skips serving)")
     args = ap.parse_args()
