@@ -279,9 +279,13 @@ eg_status eg_solve_credit_noalloc(eg_arena *arena, int32_t credit_bits, int64_t 
  * instead of waiting for them to finish.  The solve runs in slices of rounds
  * that end early when a request arrives.  After each slice, every game with
  * no work left is finished and leaves, freeing its slot and memory for the
- * queue.  The result of every request equals eg_solve_credit on its arena
- * alone (the games are disjoint in the pool; each has its own bound C and
- * weight map), computed in int64.
+ * queue.  A game still unfinished after its arena's EG_OPT_CERTIFY_AFTER
+ * rounds (while its EG_OPT_CAP_CERTIFY is on) is taken out and solved alone
+ * by eg_solve_credit's certified route; its slot is freed once the resident
+ * solve has dropped its remaining work.  The result of every request equals
+ * eg_solve_credit on its arena alone (the games are disjoint in the pool;
+ * each has its own bound C and weight map), computed in int64.  Do not solve
+ * an arena yourself while a request for it is pending.
  *
  * eg_poll returns EG_PENDING until the request is done, then copies its
  * credits (n elements: int32 if credit_bits is 32, else int64; host or

@@ -42,7 +42,13 @@ def build(force: bool = False) -> str:
         if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
             os.makedirs(_LIB_DIR, exist_ok=True)
             tmp = lib + f".tmp{os.getpid()}"
-            subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", *extra, "-o", tmp, src])
+            cmd = ["gcc", "-O2", "-std=c99", "-shared", "-fPIC", *extra, "-o", tmp, src]
+            if subprocess.run(cmd, capture_output=True).returncode != 0:
+                if not extra:
+                    subprocess.check_call(cmd)
+                # no OpenMP here: the sweep baseline builds single-threaded
+                # (it reports the threads it used)
+                subprocess.check_call([c for c in cmd if c not in extra])
             os.replace(tmp, lib)
     return _LIB
 

@@ -14,6 +14,12 @@
 // instead of waiting for the others to finish.  After each slice, a game with
 // no entry left in the round's lists is finished: its credits are copied
 // out, its ranges and slot are freed, and waiting requests take them.
+//
+// A game still unfinished after its arena's EG_OPT_CERTIFY_AFTER rounds (with
+// certified trial caps on) is taken out: it is solved alone with the trials
+// (eg_solve_credit's route), and its slot is retired -- its views get a
+// negative C, so the fixpoint kernel consumes its remaining entries without
+// work -- and freed once no entry of it is left.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -120,6 +126,12 @@ __global__ void k_unset_bits(unsigned *bits, int g0, int n) {
         atomicAnd(bits + ((g0 + i) >> 5), ~(1u << ((g0 + i) & 31)));
 }
 
+// A slot whose game was solved elsewhere, freed once its entries are gone.
+struct Retiring {
+    int slot;
+    long long vb, nv, eb, m;
+};
+
 struct Server {
     int device = 0;
     size_t budget = 0;
@@ -142,6 +154,7 @@ struct Server {
     std::vector<int> free_slots;
     std::vector<Request *> active;  // by slot
     int nactive = 0;
+    std::vector<Retiring> retiring;
     Resident R;
     long long *stage = nullptr;  // pinned staging of finished credits
     size_t stage_cap = 0;
@@ -250,9 +263,46 @@ static void complete(Server *S, std::vector<Request *> &fin) {
     fin.clear();
 }
 
+// Solves a slow resident game alone with certified trial caps, then retires
+// its slot (views with C < 0: the kernel drops its entries).
+static eg_status take_out(Server *S, Request *r, std::vector<Request *> &fin) {
+    r->credits.resize((size_t)r->ar->n);
+    eg_stats st{};
+    eg_status rc = solve(r->ar, 64, r->scale, r->shift, r->credits.data(), &st, S->stream, 0);
+    r->status = rc;
+    if (rc == EG_OK) {
+        st.credit_bits = r->credit_bits == 32 ? 32 : 64;
+        st.rounds += S->R.r - r->r_admit;
+        st.fixpoint_ms += r->dev_ms;
+        r->st = st;
+    }
+    const long long retired = -1;
+    EG_CUDA_TRY(cudaMemcpyAsync(S->R.C + r->slot, &retired, 8, cudaMemcpyHostToDevice, S->stream));
+    EG_CUDA_TRY(cudaStreamSynchronize(S->stream));
+    S->retiring.push_back(Retiring{r->slot, r->vb, (long long)r->ar->n + 1, r->eb, r->ar->m});
+    S->active[r->slot] = nullptr;
+    r->slot = -1;
+    --S->nactive;
+    fin.push_back(r);
+    return EG_OK;
+}
+
 static eg_status harvest(Server *S, std::vector<Request *> &fin) {
     eg_status rc = resident_busy(S->R, S->stream);
     if (rc != EG_OK) return rc;
+    // retired slots with no entry left are free again
+    for (size_t k = 0; k < S->retiring.size();) {
+        const Retiring t = S->retiring[k];
+        if (S->R.host_busy[t.slot]) {
+            ++k;
+            continue;
+        }
+        S->vfree.release(t.vb, t.nv);
+        S->efree.release(t.eb, t.m);
+        S->free_slots.push_back(t.slot);
+        S->retiring[k] = S->retiring.back();
+        S->retiring.pop_back();
+    }
     std::vector<Request *> ready;
     size_t total = 0;
     for (int k = 0; k < S->max_slots; ++k) {
@@ -260,6 +310,17 @@ static eg_status harvest(Server *S, std::vector<Request *> &fin) {
         if (r && !S->R.host_busy[k]) {
             ready.push_back(r);
             total += (size_t)r->ar->n;
+        }
+    }
+    // games that are slow in the resident solve go through the certified route
+    for (int k = 0; k < S->max_slots; ++k) {
+        Request *r = S->active[k];
+        if (!r || !S->R.host_busy[k]) continue;
+        const eg_arena *ar = r->ar;
+        if (ar->cap_certify > 0 && ar->warm_start && ar->certify_after > 0 &&
+            S->R.r - r->r_admit >= ar->certify_after) {
+            rc = take_out(S, r, fin);
+            if (rc != EG_OK) return rc;
         }
     }
     if (ready.empty()) return EG_OK;
@@ -300,6 +361,12 @@ static eg_status harvest(Server *S, std::vector<Request *> &fin) {
 }
 
 static void fail_active(Server *S, eg_status rc, std::vector<Request *> &fin) {
+    for (const Retiring &t : S->retiring) {  // the state is reset after a failure
+        S->vfree.release(t.vb, t.nv);
+        S->efree.release(t.eb, t.m);
+        S->free_slots.push_back(t.slot);
+    }
+    S->retiring.clear();
     for (int k = 0; k < S->max_slots; ++k) {
         Request *r = S->active[k];
         if (!r) continue;
@@ -317,7 +384,7 @@ static void worker_main(Server *S) {
         std::vector<Request *> admitted;
         {
             std::unique_lock<std::mutex> lk(S->mu);
-            S->cv.wait(lk, [&] { return S->stop || !S->queue.empty() || S->nactive > 0; });
+            S->cv.wait(lk, [&] { return S->stop || !S->queue.empty() || S->nactive > 0 || !S->retiring.empty(); });
             if (S->stop) break;
             while (!S->queue.empty() && !S->free_slots.empty()) {
                 Request *r = S->queue.front();
@@ -356,7 +423,7 @@ static void worker_main(Server *S) {
             }
         }
         complete(S, fin);
-        if (S->nactive == 0) continue;
+        if (S->nactive == 0 && S->retiring.empty()) continue;
         int dev = DEV_OK;
         cudaEventRecord(S->e0, S->stream);
         eg_status rc = resident_slice(S->R, SLICE_ROUNDS, S->stream, &dev);

@@ -95,7 +95,9 @@ struct Args {
     int local_maxdeg;   // largest degree a vertex may have to be chained locally
 };
 
-// One instance's view of the arena, carried per list entry.
+// One instance's view of the arena, carried per list entry.  A negative C
+// marks an instance whose solve was taken over elsewhere (a resident solve
+// retires it): its entries are consumed without work.
 struct View {
     int delta;
     long long scale;
@@ -497,7 +499,7 @@ __device__ __forceinline__ void push_edges(const Args<T> &a, int r, int beg, int
         const View wj = shfl_view<MULTI>(vw, j);
         unsigned need = NEED_NONE;
         int p = 0, work = 0;
-        if (act) {
+        if (act && wj.C >= 0) {
             const int e = bj + (xl - oj);
             const unsigned pr = __ldg(a.A.rcol + e);
             const int pa = (int)(pr & 0x7fffffffu);
@@ -531,15 +533,21 @@ __device__ void drain_local(const Args<T> &a, int r, T *red, Local<T> &L) {
         if (windows >= a.local_windows) L.on = false;
         ++windows;
         const int take = min(32, L.top);
-        const bool have = lane < take;
+        bool have = lane < take;
         const int raw = have ? L.stack[L.top - 1 - lane] : 0;
         __syncwarp();
         L.top -= take;
         const int g = raw & 0x7fffffff;
-        const bool is_push = have && (raw & (int)P1_FLAG);
-        const bool is_pull = have && !(raw & (int)P1_FLAG);
         View vw = idle_view<MULTI>(a);
         if (have) vw = view_of<MULTI>(a, g);
+        if (have && vw.C < 0) {  // retired instance: unmark and drop
+            atomicAnd(((raw & (int)P1_FLAG) ? a.bits_push[(r + 1) & 1] : a.bits_pull[(r + 1) & 1]) + (g >> 5),
+                      ~(1u << (g & 31)));
+            have = false;
+            vw = idle_view<MULTI>(a);
+        }
+        const bool is_push = have && (raw & (int)P1_FLAG);
+        const bool is_pull = have && !(raw & (int)P1_FLAG);
         const int v = g - vw.delta;
         if (!L.on) {  // budget spent: the entries (still marked) join the next round's lists
             const int work = !have ? 0
@@ -654,7 +662,7 @@ __device__ void pull_phase(const Args<T> &a, int r, T *red, Stager &out) {
                     atomicExch(a.acc_done + g, 0);
                 }
             }
-            if (done && res > ld_cg(a.f + g) && res > atomicMax(a.f + g, res)) {
+            if (done && vw.C >= 0 && res > ld_cg(a.f + g) && res > atomicMax(a.f + g, res)) {
                 pwork = __ldg(A.rrow_ptr + v + 1) - __ldg(A.rrow_ptr + v);
                 if (pwork > 0) {
                     const unsigned bit = 1u << (g & 31);

@@ -142,12 +142,13 @@ def test_destroy_with_pending_requests():
 
 def test_late_arrivals_join_the_running_solve():
     # a slow game (a 64 x 64 grid without certified caps takes thousands of
-    # rounds) is being solved when small games arrive: they join the
+    # rounds, and certification is off for it here) is being solved when small games arrive: they join the
     # resident solve at its next round and finish while the slow one runs,
     # and every result equals the solve of that game alone
     slow = gen.grid_game(64, 64, seed=1)
     smalls = [gen.config(1, s) for s in (2, 3, 4)] + [gen.rmat_game(10, 8, seed=5)]
     a_slow = eg.Arena(slow)
+    a_slow.tune(cap_certify=0)  # keep it in the resident solve (no certified take-over)
     a_small = [eg.Arena(g) for g in smalls]
     server = eg.eg_server_create(2 << 30, 8)
     try:
@@ -170,4 +171,30 @@ def test_late_arrivals_join_the_running_solve():
         eg.eg_server_destroy(server)
         a_slow.close()
         for a in a_small:
+            a.close()
+
+
+def test_slow_games_are_taken_out_to_the_certified_route():
+    # grids stay unfinished past EG_OPT_CERTIFY_AFTER rounds in the resident
+    # solve; the server solves them alone with certified trial caps, retires
+    # their slots, and keeps serving the others
+    hard = [gen.grid_game(48, 48, seed=2), gen.grid_game(40, 64, seed=5)]
+    easy = [gen.config(1, 7), gen.rmat_game(11, 8, seed=3)]
+    games = hard + easy
+    arenas = [eg.Arena(g) for g in games]
+    want = [alone(a.handle, 0, 1, 0, g.n) for g, a in zip(games, arenas)]
+    server = eg.eg_server_create(1 << 30, 4)
+    try:
+        for rep in range(2):  # the second pass reuses slots freed by retirement
+            ts = [eg.eg_submit(server, a.handle, 0, 1, 0) for a in arenas]
+            for i, t in enumerate(ts):
+                out = np.empty(games[i].n, dtype=np.int64)
+                rc, st = wait(server, t, out, timeout=120)
+                assert rc == eg.EG_OK, eg.eg_last_error()
+                np.testing.assert_array_equal(out, want[i])
+                if i < len(hard):
+                    assert st.seeded > 0  # proven player-1 vertices: the certified route ran
+    finally:
+        eg.eg_server_destroy(server)
+        for a in arenas:
             a.close()
