@@ -178,6 +178,32 @@ __device__ __forceinline__ void for_rows_of_tier(int n, const int *row_ptr, int 
 
 __global__ void k_scatter(int n, const int *row_ptr, const int *col, const int *w, const unsigned *owner_bits,
                           int *fill, unsigned *rcol, int *rw, int tier) {
+    if (tier == 0) {
+        // one thread per short row; its (at most TIER0) cursor atomics are
+        // independent, so all of them are in flight at once
+        for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+            const int b = row_ptr[v], deg = row_ptr[v + 1] - b;
+            if (row_tier(deg) != 0) continue;
+            const unsigned tag = owner_tag(owner_bits, v);
+            int dst[TIER0], wt[TIER0], slot[TIER0];
+#pragma unroll
+            for (int k = 0; k < TIER0; ++k)
+                if (k < deg) {
+                    dst[k] = col[b + k];
+                    wt[k] = w[b + k];
+                }
+#pragma unroll
+            for (int k = 0; k < TIER0; ++k)
+                if (k < deg) slot[k] = atomicAdd(fill + dst[k], 1);
+#pragma unroll
+            for (int k = 0; k < TIER0; ++k)
+                if (k < deg) {
+                    rcol[slot[k]] = tag;
+                    rw[slot[k]] = wt[k];
+                }
+        }
+        return;
+    }
     for_rows_of_tier(n, row_ptr, tier, [&](int v, int b, int e, int first, int step) {
         const unsigned tag = owner_tag(owner_bits, v);
         for (int k = b + first; k < e; k += step) scatter_edge(k, tag, col, w, fill, rcol, rw);
@@ -188,6 +214,23 @@ __global__ void k_scatter(int n, const int *row_ptr, const int *col, const int *
 // Tier 0 writes directly; tiers 1 and 2 combine with atomics on outputs that
 // start at (INT_MAX, INT_MIN).
 __global__ void k_row_extremes(int n, const int *row_ptr, const int *w, int *wmin, int *wmax, int tier) {
+    if (tier == 0) {  // one thread per short row, its loads all in flight at once
+        for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+            const int b = row_ptr[v], deg = row_ptr[v + 1] - b;
+            if (row_tier(deg) != 0) continue;
+            int lo = 0x7fffffff, hi = (int)0x80000000;
+#pragma unroll
+            for (int k = 0; k < TIER0; ++k)
+                if (k < deg) {
+                    const int x = w[b + k];
+                    lo = min(lo, x);
+                    hi = max(hi, x);
+                }
+            wmin[v] = lo;
+            wmax[v] = hi;
+        }
+        return;
+    }
     for_rows_of_tier(n, row_ptr, tier, [&](int v, int b, int e, int first, int step) {
         int lo = 0x7fffffff, hi = (int)0x80000000;
         for (int k = b + first; k < e; k += step) {
@@ -198,6 +241,67 @@ __global__ void k_row_extremes(int n, const int *row_ptr, const int *w, int *wmi
             wmin[v] = lo;
             wmax[v] = hi;
             return;
+        }
+        for (int d = 16; d; d >>= 1) {
+            lo = min(lo, __shfl_xor_sync(FULL, lo, d));
+            hi = max(hi, __shfl_xor_sync(FULL, hi, d));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(wmin + v, lo);
+            atomicMax(wmax + v, hi);
+        }
+    });
+}
+
+// Rows longer than TIER0 edges, collected into two global lists (tier 1:
+// up to TIER1 edges, tier 2: longer), so that their work spreads over the
+// whole grid: R-MAT hubs sit at small vertex ids, and a per-chunk split
+// would leave them to a few blocks.
+__global__ void k_collect_rows(int n, const int *row_ptr, int *list1, int *cnt1, int *list2, int *cnt2) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int t = row_tier(row_ptr[v + 1] - row_ptr[v]);
+        if (t == 1) list1[atomicAdd(cnt1, 1)] = v;
+        else if (t == 2) list2[atomicAdd(cnt2, 1)] = v;
+    }
+}
+
+// fn(v, begin, end, first, step) over the collected long rows: a tier-1 row
+// to one warp of the grid (round robin), a tier-2 row to every thread of the
+// grid in turn.
+template <typename F>
+__device__ __forceinline__ void for_long_rows(const int *row_ptr, const int *list1, const int *cnt1,
+                                              const int *list2, const int *cnt2, F fn) {
+    const int lane = threadIdx.x & 31;
+    const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int c1 = *cnt1, c2 = *cnt2;
+    for (int k = gwarp; k < c1; k += nwarps) {
+        const int v = list1[k];
+        fn(v, row_ptr[v], row_ptr[v + 1], lane, 32);
+    }
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    for (int k = 0; k < c2; ++k) {
+        const int v = list2[k];
+        fn(v, row_ptr[v], row_ptr[v + 1], gt, nt);
+    }
+}
+
+__global__ void k_scatter_long(const int *row_ptr, const int *col, const int *w, const unsigned *owner_bits,
+                               const int *list1, const int *cnt1, const int *list2, const int *cnt2, int *fill,
+                               unsigned *rcol, int *rw) {
+    for_long_rows(row_ptr, list1, cnt1, list2, cnt2, [&](int v, int b, int e, int first, int step) {
+        const unsigned tag = owner_tag(owner_bits, v);
+        for (int k = b + first; k < e; k += step) scatter_edge(k, tag, col, w, fill, rcol, rw);
+    });
+}
+
+// Weight extremes of the long rows; wmin / wmax start at (INT_MAX, INT_MIN).
+__global__ void k_row_extremes_long(const int *row_ptr, const int *w, const int *list1, const int *cnt1,
+                                    const int *list2, const int *cnt2, int *wmin, int *wmax) {
+    for_long_rows(row_ptr, list1, cnt1, list2, cnt2, [&](int v, int b, int e, int first, int step) {
+        int lo = 0x7fffffff, hi = (int)0x80000000;
+        for (int k = b + first; k < e; k += step) {
+            lo = min(lo, w[k]);
+            hi = max(hi, w[k]);
         }
         for (int d = 16; d; d >>= 1) {
             lo = min(lo, __shfl_xor_sync(FULL, lo, d));
@@ -254,6 +358,12 @@ __global__ void k_hash_rev(int n, const int *rrow_ptr, const unsigned *rcol, con
 }
 
 static size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+static int num_sms_arena(int device) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    return sms > 0 ? sms : 1;
+}
 
 static bool is_device_ptr(const void *p) {
     cudaPointerAttributes attr{};
@@ -365,6 +475,10 @@ static eg_status create(int64_t n64, int64_t m64, const int64_t *row_ptr, const 
         const size_t t_flags = t; t = align_up(t + 64);
         const size_t t_scan = t; t = align_up(t + ((size_t)n / 1024 + 64) * 4 * 2);
         const size_t t_fill = t; t = align_up(t + ((size_t)n + 1) * 4);
+        // long-row lists: tier 1 (at most n rows), tier 2 (rows of more than
+        // TIER1 edges: at most m / (TIER1 + 1)), then their two counts
+        const size_t n_list2 = (size_t)m / (TIER1 + 1) + 1;
+        const size_t t_list = t; t = align_up(t + ((size_t)n + n_list2 + 2) * 4);
         TRY(cudaMalloc((void **)&tmp, t));
         long long *rp64 = (long long *)(tmp + t_rp);
         long long *rrp64 = (long long *)(tmp + t_rrp);
@@ -372,6 +486,9 @@ static eg_status create(int64_t n64, int64_t m64, const int64_t *row_ptr, const 
         unsigned long long *dhash = (unsigned long long *)(tmp + t_flags + 16);
         int *scan_scratch = (int *)(tmp + t_scan);
         int *fill = (int *)(tmp + t_fill);
+        int *list1 = (int *)(tmp + t_list);
+        int *list2 = list1 + n;
+        int *long_cnt = list2 + n_list2;
 
         TRY(cudaMemsetAsync(dflags, 0, 64, s));
         TRY(cudaMemcpyAsync(rp64, row_ptr, ((size_t)n + 1) * 8, kind, s));
@@ -422,8 +539,11 @@ static eg_status create(int64_t n64, int64_t m64, const int64_t *row_ptr, const 
                 const int gt = (int)std::min<long long>(((long long)n + 255) / 256, 1 << 14);
                 const int gw = (int)std::min<long long>(((long long)n + 7) / 8, 1 << 14);
                 k_scatter<<<gt, 256, 0, s>>>(n, rp32, dcol, dw, down, fill, drcol, drw, 0);
-                k_scatter<<<gt, 256, 0, s>>>(n, rp32, dcol, dw, down, fill, drcol, drw, 1);
-                k_scatter<<<gt, 256, 0, s>>>(n, rp32, dcol, dw, down, fill, drcol, drw, 2);
+                TRY(cudaMemsetAsync(long_cnt, 0, 8, s));
+                k_collect_rows<<<gt, 256, 0, s>>>(n, rp32, list1, long_cnt, list2, long_cnt + 1);
+                k_scatter_long<<<num_sms_arena(a->device) * 8, 256, 0, s>>>(rp32, dcol, dw, down, list1, long_cnt,
+                                                                            list2, long_cnt + 1, fill,
+                                                                            drcol, drw);
                 TRY(cudaGetLastError());
             } else {
                 const int gw = (int)std::min<long long>(((long long)n + 7) / 8, 1 << 16);
@@ -439,8 +559,12 @@ static eg_status create(int64_t n64, int64_t m64, const int64_t *row_ptr, const 
                 k_fill_int<<<gt, 256, 0, s>>>(dwmin, n, 0x7fffffff);
                 k_fill_int<<<gt, 256, 0, s>>>(dwmax, n, (int)0x80000000);
                 k_row_extremes<<<gt, 256, 0, s>>>(n, rp32, dw, dwmin, dwmax, 0);
-                k_row_extremes<<<gt, 256, 0, s>>>(n, rp32, dw, dwmin, dwmax, 1);
-                k_row_extremes<<<gt, 256, 0, s>>>(n, rp32, dw, dwmin, dwmax, 2);
+                if (have_rev) {  // the long-row lists are made by the reverse build otherwise
+                    TRY(cudaMemsetAsync(long_cnt, 0, 8, s));
+                    k_collect_rows<<<gt, 256, 0, s>>>(n, rp32, list1, long_cnt, list2, long_cnt + 1);
+                }
+                k_row_extremes_long<<<num_sms_arena(a->device) * 8, 256, 0, s>>>(
+                    rp32, dw, list1, long_cnt, list2, long_cnt + 1, dwmin, dwmax);
                 TRY(cudaGetLastError());
             }
             TRY(cudaStreamSynchronize(s));
