@@ -117,10 +117,10 @@ static cudaError_t exclusive_scan(int *data, int len, int *scratch, cudaStream_t
     return cudaGetLastError();
 }
 
-// Row work is split by degree so that hubs do not serialise: tier 0 gives a
-// row of at most TIER0 edges to one thread, tier 1 a row of at most TIER1
-// edges to one warp, tier 2 a longer row to a whole block.  Each tiered
-// kernel visits every row and skips the rows of the other tiers.
+// Row work is split by degree so that hubs do not serialise: a row of at
+// most TIER0 edges goes to one thread; longer rows are collected into
+// grid-wide lists, a row of at most TIER1 edges to one warp, a longer one to
+// a whole block (k_collect_rows, for_long_rows).
 constexpr int TIER0 = 16;
 constexpr int TIER1 = 2048;
 
@@ -138,119 +138,52 @@ __device__ __forceinline__ unsigned owner_tag(const unsigned *owner_bits, int v)
     return (unsigned)v | ((((owner_bits[v >> 5] >> (v & 31)) & 1u) != 0) ? P1_FLAG : 0u);
 }
 
-// Tiered row loop: tier 0 gives each thread one row; tiers 1 and 2 first
-// collect the rows of their tier from a chunk of blockDim.x rows into shared
-// memory, then give each collected row to a warp (tier 1) or to the whole
-// block (tier 2).  fn(v, begin, step) visits edges begin, begin+step, ...
-template <typename F>
-__device__ __forceinline__ void for_rows_of_tier(int n, const int *row_ptr, int tier, F fn) {
-    __shared__ int rows[1024];
-    __shared__ int nrows;
-    if (tier == 0) {
-        for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-            const int b = row_ptr[v], e = row_ptr[v + 1];
-            if (row_tier(e - b) == 0) fn(v, b, e, 0, 1);
-        }
-        return;
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
-        if (threadIdx.x == 0) nrows = 0;
-        __syncthreads();
-        const int v = base + threadIdx.x;
-        if (v < n && row_tier(row_ptr[v + 1] - row_ptr[v]) == tier) rows[atomicAdd(&nrows, 1)] = v;
-        __syncthreads();
-        const int cnt = nrows;
-        if (tier == 1) {
-            for (int k = wid; k < cnt; k += nwarp) {
-                const int u = rows[k];
-                fn(u, row_ptr[u], row_ptr[u + 1], lane, 32);
-            }
-        } else {
-            for (int k = 0; k < cnt; ++k) {
-                const int u = rows[k];
-                fn(u, row_ptr[u], row_ptr[u + 1], (int)threadIdx.x, (int)blockDim.x);
-            }
-        }
-        __syncthreads();
-    }
-}
-
+// Scatter of the short rows (at most TIER0 edges) into the reverse CSR: one
+// thread per row, all of its cursor atomics in flight at once.  Longer rows
+// go through k_collect_rows / k_scatter_long.
 __global__ void k_scatter(int n, const int *row_ptr, const int *col, const int *w, const unsigned *owner_bits,
-                          int *fill, unsigned *rcol, int *rw, int tier) {
-    if (tier == 0) {
-        // one thread per short row; its (at most TIER0) cursor atomics are
-        // independent, so all of them are in flight at once
-        for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-            const int b = row_ptr[v], deg = row_ptr[v + 1] - b;
-            if (row_tier(deg) != 0) continue;
-            const unsigned tag = owner_tag(owner_bits, v);
-            int dst[TIER0], wt[TIER0], slot[TIER0];
-#pragma unroll
-            for (int k = 0; k < TIER0; ++k)
-                if (k < deg) {
-                    dst[k] = col[b + k];
-                    wt[k] = w[b + k];
-                }
-#pragma unroll
-            for (int k = 0; k < TIER0; ++k)
-                if (k < deg) slot[k] = atomicAdd(fill + dst[k], 1);
-#pragma unroll
-            for (int k = 0; k < TIER0; ++k)
-                if (k < deg) {
-                    rcol[slot[k]] = tag;
-                    rw[slot[k]] = wt[k];
-                }
-        }
-        return;
-    }
-    for_rows_of_tier(n, row_ptr, tier, [&](int v, int b, int e, int first, int step) {
+                          int *fill, unsigned *rcol, int *rw) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int b = row_ptr[v], deg = row_ptr[v + 1] - b;
+        if (row_tier(deg) != 0) continue;
         const unsigned tag = owner_tag(owner_bits, v);
-        for (int k = b + first; k < e; k += step) scatter_edge(k, tag, col, w, fill, rcol, rw);
-    });
+        int dst[TIER0], wt[TIER0], slot[TIER0];
+#pragma unroll
+        for (int k = 0; k < TIER0; ++k)
+            if (k < deg) {
+                dst[k] = col[b + k];
+                wt[k] = w[b + k];
+            }
+#pragma unroll
+        for (int k = 0; k < TIER0; ++k)
+            if (k < deg) slot[k] = atomicAdd(fill + dst[k], 1);
+#pragma unroll
+        for (int k = 0; k < TIER0; ++k)
+            if (k < deg) {
+                rcol[slot[k]] = tag;
+                rw[slot[k]] = wt[k];
+            }
+    }
 }
 
-// Smallest and largest weight of every row (rows are never empty here).
-// Tier 0 writes directly; tiers 1 and 2 combine with atomics on outputs that
-// start at (INT_MAX, INT_MIN).
-__global__ void k_row_extremes(int n, const int *row_ptr, const int *w, int *wmin, int *wmax, int tier) {
-    if (tier == 0) {  // one thread per short row, its loads all in flight at once
-        for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-            const int b = row_ptr[v], deg = row_ptr[v + 1] - b;
-            if (row_tier(deg) != 0) continue;
-            int lo = 0x7fffffff, hi = (int)0x80000000;
-#pragma unroll
-            for (int k = 0; k < TIER0; ++k)
-                if (k < deg) {
-                    const int x = w[b + k];
-                    lo = min(lo, x);
-                    hi = max(hi, x);
-                }
-            wmin[v] = lo;
-            wmax[v] = hi;
-        }
-        return;
-    }
-    for_rows_of_tier(n, row_ptr, tier, [&](int v, int b, int e, int first, int step) {
+// Smallest and largest weight of every short row (rows are never empty
+// here): one thread per row, its loads all in flight at once.  Longer rows go
+// through k_row_extremes_long.
+__global__ void k_row_extremes(int n, const int *row_ptr, const int *w, int *wmin, int *wmax) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int b = row_ptr[v], deg = row_ptr[v + 1] - b;
+        if (row_tier(deg) != 0) continue;
         int lo = 0x7fffffff, hi = (int)0x80000000;
-        for (int k = b + first; k < e; k += step) {
-            lo = min(lo, w[k]);
-            hi = max(hi, w[k]);
-        }
-        if (step == 1) {
-            wmin[v] = lo;
-            wmax[v] = hi;
-            return;
-        }
-        for (int d = 16; d; d >>= 1) {
-            lo = min(lo, __shfl_xor_sync(FULL, lo, d));
-            hi = max(hi, __shfl_xor_sync(FULL, hi, d));
-        }
-        if ((threadIdx.x & 31) == 0) {
-            atomicMin(wmin + v, lo);
-            atomicMax(wmax + v, hi);
-        }
-    });
+#pragma unroll
+        for (int k = 0; k < TIER0; ++k)
+            if (k < deg) {
+                const int x = w[b + k];
+                lo = min(lo, x);
+                hi = max(hi, x);
+            }
+        wmin[v] = lo;
+        wmax[v] = hi;
+    }
 }
 
 // Rows longer than TIER0 edges, collected into two global lists (tier 1:
@@ -266,8 +199,7 @@ __global__ void k_collect_rows(int n, const int *row_ptr, int *list1, int *cnt1,
 }
 
 // fn(v, begin, end, first, step) over the collected long rows: a tier-1 row
-// to one warp of the grid (round robin), a tier-2 row to every thread of the
-// grid in turn.
+// to one warp of the grid, a tier-2 row to one block, both round robin.
 template <typename F>
 __device__ __forceinline__ void for_long_rows(const int *row_ptr, const int *list1, const int *cnt1,
                                               const int *list2, const int *cnt2, F fn) {
@@ -278,10 +210,9 @@ __device__ __forceinline__ void for_long_rows(const int *row_ptr, const int *lis
         const int v = list1[k];
         fn(v, row_ptr[v], row_ptr[v + 1], lane, 32);
     }
-    const int gt = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
-    for (int k = 0; k < c2; ++k) {
+    for (int k = blockIdx.x; k < c2; k += gridDim.x) {
         const int v = list2[k];
-        fn(v, row_ptr[v], row_ptr[v + 1], gt, nt);
+        fn(v, row_ptr[v], row_ptr[v + 1], (int)threadIdx.x, (int)blockDim.x);
     }
 }
 
@@ -307,7 +238,7 @@ __global__ void k_row_extremes_long(const int *row_ptr, const int *w, const int 
             lo = min(lo, __shfl_xor_sync(FULL, lo, d));
             hi = max(hi, __shfl_xor_sync(FULL, hi, d));
         }
-        if ((threadIdx.x & 31) == 0) {
+        if ((threadIdx.x & 31) == 0 && lo <= hi) {  // the warp saw an edge of the row
             atomicMin(wmin + v, lo);
             atomicMax(wmax + v, hi);
         }
@@ -479,7 +410,9 @@ static eg_status create(int64_t n64, int64_t m64, const int64_t *row_ptr, const 
         // TIER1 edges: at most m / (TIER1 + 1)), then their two counts
         const size_t n_list2 = (size_t)m / (TIER1 + 1) + 1;
         const size_t t_list = t; t = align_up(t + ((size_t)n + n_list2 + 2) * 4);
-        TRY(cudaMalloc((void **)&tmp, t));
+        // the pinned control block of the arena doubles as the host side of the checks
+        TRY(cudaMallocHost(&a->host_ctrl, sizeof(Ctrl)));
+        TRY(cudaMallocAsync((void **)&tmp, t, s));
         long long *rp64 = (long long *)(tmp + t_rp);
         long long *rrp64 = (long long *)(tmp + t_rrp);
         unsigned *dflags = (unsigned *)(tmp + t_flags);
@@ -509,12 +442,10 @@ static eg_status create(int64_t n64, int64_t m64, const int64_t *row_ptr, const 
                 k_check_cols<<<ge, 256, 0, s>>>((const int *)drcol, m, n, dflags, BAD_RCOL);
                 TRY(cudaGetLastError());
             }
-            TRY(cudaMallocHost((void **)&hflags, 16));
+            hflags = (unsigned *)a->host_ctrl;
             TRY(cudaMemcpyAsync(hflags, dflags, 8, cudaMemcpyDeviceToHost, s));
             TRY(cudaStreamSynchronize(s));
             const unsigned fl = hflags[0], rfl = hflags[1] & BAD_ROWPTR;
-            cudaFreeHost(hflags);
-            hflags = nullptr;
             if (fl & (BAD_ROWPTR | BAD_COL)) {
                 set_error("malformed forward CSR (%s)", (fl & BAD_ROWPTR) ? "row_ptr" : "col out of range");
                 rc = EG_ERR_INVALID;
@@ -538,7 +469,7 @@ static eg_status create(int64_t n64, int64_t m64, const int64_t *row_ptr, const 
                 TRY(cudaMemcpyAsync(fill, rrp32, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
                 const int gt = (int)std::min<long long>(((long long)n + 255) / 256, 1 << 14);
                 const int gw = (int)std::min<long long>(((long long)n + 7) / 8, 1 << 14);
-                k_scatter<<<gt, 256, 0, s>>>(n, rp32, dcol, dw, down, fill, drcol, drw, 0);
+                k_scatter<<<gt, 256, 0, s>>>(n, rp32, dcol, dw, down, fill, drcol, drw);
                 TRY(cudaMemsetAsync(long_cnt, 0, 8, s));
                 k_collect_rows<<<gt, 256, 0, s>>>(n, rp32, list1, long_cnt, list2, long_cnt + 1);
                 k_scatter_long<<<num_sms_arena(a->device) * 8, 256, 0, s>>>(rp32, dcol, dw, down, list1, long_cnt,
@@ -558,7 +489,7 @@ static eg_status create(int64_t n64, int64_t m64, const int64_t *row_ptr, const 
                 const int gw = (int)std::min<long long>(((long long)n + 7) / 8, 1 << 14);
                 k_fill_int<<<gt, 256, 0, s>>>(dwmin, n, 0x7fffffff);
                 k_fill_int<<<gt, 256, 0, s>>>(dwmax, n, (int)0x80000000);
-                k_row_extremes<<<gt, 256, 0, s>>>(n, rp32, dw, dwmin, dwmax, 0);
+                k_row_extremes<<<gt, 256, 0, s>>>(n, rp32, dw, dwmin, dwmax);
                 if (have_rev) {  // the long-row lists are made by the reverse build otherwise
                     TRY(cudaMemsetAsync(long_cnt, 0, 8, s));
                     k_collect_rows<<<gt, 256, 0, s>>>(n, rp32, list1, long_cnt, list2, long_cnt + 1);
@@ -567,9 +498,9 @@ static eg_status create(int64_t n64, int64_t m64, const int64_t *row_ptr, const 
                     rp32, dw, list1, long_cnt, list2, long_cnt + 1, dwmin, dwmax);
                 TRY(cudaGetLastError());
             }
-            TRY(cudaStreamSynchronize(s));
-            cudaFree(tmp);
+            TRY(cudaFreeAsync(tmp, s));
             tmp = nullptr;
+            TRY(cudaStreamSynchronize(s));
             if (have_rev && hh[0] != hh[1]) {
                 set_error("reverse CSR does not hold the same edges as the forward CSR");
                 rc = EG_ERR_INVALID;
@@ -590,7 +521,6 @@ static eg_status create(int64_t n64, int64_t m64, const int64_t *row_ptr, const 
         TRY(cudaEventCreate(&a->ev0));
         TRY(cudaEventCreate(&a->ev1));
         TRY(cudaEventCreate(&a->evk));
-        TRY(cudaMallocHost(&a->host_ctrl, sizeof(Ctrl)));
         long long C = 0, wm = 0;
         rc = compute_bound(a, 1, 0, &C, &wm, s);
         if (rc != EG_OK) goto fail;
@@ -599,7 +529,10 @@ static eg_status create(int64_t n64, int64_t m64, const int64_t *row_ptr, const 
     *out = a;
     return EG_OK;
 fail:
-    if (tmp) cudaFree(tmp);
+    if (tmp) {
+        cudaFreeAsync(tmp, 0);
+        cudaStreamSynchronize(0);
+    }
     destroy(a);
     return rc;
 }
