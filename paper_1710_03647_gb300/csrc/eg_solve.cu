@@ -181,59 +181,112 @@ __global__ void k_fill(T *p, long long n, T v) {
 // can keep the play on that cycle forever, so every credit runs out
 // (Lemma "EGcycles" with memoryless determinacy, Sec. 3).  Its least-EPM
 // value is TOP, so starting it at TOP stays below the least fixpoint.
-// Looked for: negative self-loops and 2-cycles u -> t -> u.  One warp per
-// player-1 credit compares each out-edge (u, t) with each in-edge (s, u)
-// for s == t; vertices with out-degree x in-degree above max_pairs are
-// skipped (the warm start is optional, missing a cycle only costs time).
+// Looked for: negative self-loops and 2-cycles u -> t -> u with t a player-1
+// vertex.  A vertex whose out- and in-degree are both at most
+// SEED_LANE_DEG is checked by one lane alone (its in-edges held in registers,
+// every load independent); a larger one by the whole warp, which compares
+// each out-edge (u, t) with each in-edge (s, u) for s == t.  Vertices with
+// out-degree x in-degree above max_pairs are skipped (the warm start is
+// optional, missing a cycle only costs time).
+constexpr int SEED_LANE_DEG = 8;
+
 template <bool MULTI, typename T>
 __global__ void k_seed(Args<T> a, long long max_pairs, unsigned *seed_bits, unsigned long long *count, int g0,
                        int g1) {
     const DevArena &A = a.A;
     const int lane = lane_id();
-    const int nw = gridDim.x * (blockDim.x >> 5);
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
     unsigned found_total = 0;
-    for (int g = g0 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); g < g1; g += nw) {
-        if (!in_active<MULTI>(a, g)) continue;
-        const View vw = view_of<MULTI>(a, g);
-        const int u = g - vw.delta;
-        if (!(((__ldg(A.owner_bits + (u >> 5)) >> (u & 31)) & 1u) ^ a.inv)) continue;
-        const int ob = __ldg(A.row_ptr + u), oe = __ldg(A.row_ptr + u + 1);
-        const int ib = __ldg(A.rrow_ptr + u), ie = __ldg(A.rrow_ptr + u + 1);
-        if ((long long)(oe - ob) * (long long)(ie - ib) > max_pairs) continue;
-        bool found = false;
-        for (int kb = ob; kb < oe; kb += 32) {
-            const int k = kb + lane;
-            int t = -1;
-            long long wt = 0;
-            if (k < oe) {
-                t = __ldg(A.col + k);
-                wt = wmapv(__ldg(A.w + k), vw);
-                if (t == u && wt < 0) found = true;  // negative self-loop
+    for (int base = g0 + gw * 32; base < g1; base += nw * 32) {
+        const int g = base + lane;
+        bool mine = false;  // a player-1 credit of this lane, within max_pairs
+        View vw = idle_view<MULTI>(a);
+        int u = 0, ob = 0, oe = 0, ib = 0, ie = 0;
+        if (g < g1 && in_active<MULTI>(a, g)) {
+            vw = view_of<MULTI>(a, g);
+            u = g - vw.delta;
+            if (((__ldg(A.owner_bits + (u >> 5)) >> (u & 31)) & 1u) ^ a.inv) {
+                ob = __ldg(A.row_ptr + u);
+                oe = __ldg(A.row_ptr + u + 1);
+                ib = __ldg(A.rrow_ptr + u);
+                ie = __ldg(A.rrow_ptr + u + 1);
+                mine = (long long)(oe - ob) * (long long)(ie - ib) <= max_pairs;
             }
-            for (int jb = ib; jb < ie; jb += 32) {
-                const int j = jb + lane;
-                unsigned sv = 0;
-                long long ws = 0;
-                if (j < ie) {
-                    sv = __ldg(A.rcol + j);
-                    ws = wmapv(__ldg(A.rw + j), vw);
+        }
+        const bool small = mine && oe - ob <= SEED_LANE_DEG && ie - ib <= SEED_LANE_DEG;
+        bool found = false;
+        if (small) {
+            unsigned sv[SEED_LANE_DEG];
+            long long ws[SEED_LANE_DEG];
+#pragma unroll
+            for (int j = 0; j < SEED_LANE_DEG; ++j) {
+                sv[j] = 0;
+                ws[j] = 0;
+                if (ib + j < ie) {
+                    sv[j] = __ldg(A.rcol + ib + j);
+                    ws[j] = wmapv(__ldg(A.rw + ib + j), vw);
                 }
-                const int cnt = min(32, ie - jb);
-                for (int q = 0; q < cnt; ++q) {
-                    const unsigned sq = __shfl_sync(FULL, sv, q);
-                    const long long wq = __shfl_sync(FULL, ws, q);
-                    if (((sq & P1_FLAG) != 0) != (a.inv != 0) && (int)(sq & 0x7fffffffu) == t &&
-                        (int)(sq & 0x7fffffffu) != u &&
-                        wt + wq < 0)
-                        found = true;
+            }
+#pragma unroll
+            for (int k = 0; k < SEED_LANE_DEG; ++k) {
+                if (ob + k < oe) {
+                    const int t = __ldg(A.col + ob + k);
+                    const long long wt = wmapv(__ldg(A.w + ob + k), vw);
+                    if (t == u && wt < 0) found = true;  // negative self-loop
+#pragma unroll
+                    for (int j = 0; j < SEED_LANE_DEG; ++j)
+                        if (ib + j < ie && ((sv[j] & P1_FLAG) != 0) != (a.inv != 0) &&
+                            (int)(sv[j] & 0x7fffffffu) == t && t != u && wt + ws[j] < 0)
+                            found = true;
                 }
             }
         }
-        if (__any_sync(FULL, found)) {
-            if (lane == 0) atomicOr(seed_bits + (g >> 5), 1u << (g & 31));
+        // the larger ones, one at a time by the whole warp
+        unsigned big = __ballot_sync(FULL, mine && !small);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1;
+            const int bu = __shfl_sync(FULL, u, src);
+            const int bob = __shfl_sync(FULL, ob, src), boe = __shfl_sync(FULL, oe, src);
+            const int bib = __shfl_sync(FULL, ib, src), bie = __shfl_sync(FULL, ie, src);
+            const View bv = shfl_view<MULTI>(vw, src);
+            bool bfound = false;
+            for (int kb = bob; kb < boe; kb += 32) {
+                const int k = kb + lane;
+                int t = -1;
+                long long wt = 0;
+                if (k < boe) {
+                    t = __ldg(A.col + k);
+                    wt = wmapv(__ldg(A.w + k), bv);
+                    if (t == bu && wt < 0) bfound = true;  // negative self-loop
+                }
+                for (int jb = bib; jb < bie; jb += 32) {
+                    const int j = jb + lane;
+                    unsigned sj = 0;
+                    long long wj = 0;
+                    if (j < bie) {
+                        sj = __ldg(A.rcol + j);
+                        wj = wmapv(__ldg(A.rw + j), bv);
+                    }
+                    const int cnt = min(32, bie - jb);
+                    for (int q = 0; q < cnt; ++q) {
+                        const unsigned sq = __shfl_sync(FULL, sj, q);
+                        const long long wq = __shfl_sync(FULL, wj, q);
+                        if (((sq & P1_FLAG) != 0) != (a.inv != 0) && (int)(sq & 0x7fffffffu) == t && t != bu &&
+                            wt + wq < 0)
+                            bfound = true;
+                    }
+                }
+            }
+            if (__any_sync(FULL, bfound) && lane == src) found = true;
+        }
+        if (found) {
+            atomicOr(seed_bits + (g >> 5), 1u << (g & 31));
             ++found_total;
         }
     }
+    for (int d = 16; d; d >>= 1) found_total += __shfl_down_sync(FULL, found_total, d);
     if (lane == 0 && found_total) atomicAdd(count, (unsigned long long)found_total);
 }
 
