@@ -46,14 +46,39 @@ def algorithmic_bytes(st, s):
     return st["relaxations"] * (8 + s) + (st["lifts"] + st["pushes"]) * (12 + s) + st["enqueues"] * 8
 
 
+def strip_comments(src):
+    """C/C++ source without // and /* */ comments (string and character
+    literals kept), so that a comment edit does not count as a kernel change."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return "".join(out)
+
+
 def kernel_source_hash():
-    """SHA-256 over the sources the fixpoint kernel is compiled from."""
+    """SHA-256 over the sources the fixpoint kernel is compiled from, comments
+    stripped."""
     import hashlib
 
     h = hashlib.sha256()
     for name in ("eg_solve.cu", "eg_device.cuh", "eg_internal.h"):
-        with open(os.path.join(ROOT, "paper_1710_03647_gb300", "csrc", name), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1710_03647_gb300", "csrc", name)) as fh:
+            h.update(strip_comments(fh.read()).encode())
     return h.hexdigest()
 
 

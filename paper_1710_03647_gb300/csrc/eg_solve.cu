@@ -32,6 +32,22 @@
 // entries in windows of 32.  A player-0 lift cut by a warp boundary merges
 // its partial minima through per-vertex scratch (acc, acc_done); the warp
 // that completes the count finishes the lift.
+//
+// The lift starts from f = 0 except at warm-start vertices, which start at
+// TOP (k_seed, and the proofs of the certified trials); every start is at or
+// below the least fixpoint, so the argument above still gives the least one.
+//
+// What the file holds, in order:
+//   kernels      k_bound, k_seed (warm start), k_init, the pull and push
+//                phases with per-warp local worklists, k_fixpoint
+//   solve        one game (eg_solve_credit): a first attempt with a short
+//                round budget, then certified trial caps (dual lifts with
+//                swapped owners, capped lifts, k_mark_finite,
+//                k_count_undecided) if the game needs them
+//   plans        batched solves of many instances in one launch (eg_plan_*),
+//                with per-instance certified trials
+//   resident     the resident solve behind the server (eg_server.cu)
+//   noalloc      eg_solve_credit_noalloc over a fixed device array
 #include <cuda_runtime.h>
 #include <stdio.h>
 

@@ -1,0 +1,47 @@
+"""CPU tests of bench.py's host-side helpers: the comment-insensitive hash
+that ties the ncu traffic record to the kernel sources, and the clock
+summary over the timed window."""
+from __future__ import annotations
+
+import json
+import os
+
+import bench
+
+
+def test_strip_comments_keeps_code_and_literals():
+    src = 'int a = 1; // note\n/* block\n */ const char *s = "a//b /* q */"; char c = \'/\'; char e = \'\\\'\';\n'
+    out = bench.strip_comments(src)
+    assert "note" not in out and "block" not in out
+    assert '"a//b /* q */"' in out and "'/'" in out and "'\\''" in out
+    assert "int a = 1;" in out
+
+
+def test_comment_edit_keeps_the_hash_code_edit_changes_it():
+    code = "__global__ void k(int *p) { p[0] = 1; }\n"
+    h1 = bench.strip_comments("// first version\n" + code)
+    h2 = bench.strip_comments("/* reworded */\n" + code)
+    assert h1.strip() == h2.strip()
+    assert bench.strip_comments(code.replace("= 1", "= 2")) != bench.strip_comments(code)
+
+
+def test_traffic_record_names_a_kernel_hash_and_bytes():
+    p = os.path.join(bench.ROOT, "profiles", "fixpoint_rmat20_traffic.json")
+    rec = json.load(open(p))
+    assert rec["dram_bytes_per_launch"] == rec["dram_bytes_read"] + rec["dram_bytes_write"] > 0
+    assert len(rec["kernel_source_sha256"]) == 64
+    assert rec["command"].startswith("ncu ") and "--clock-control none" in rec["command"]
+
+
+def test_clock_summary_prefers_samples_inside_the_timed_window():
+    clk = bench.ClockSampler(0)
+    row = lambda mhz, slow="Not Active": ["0", str(mhz), "2070", "900", "0x0", slow, "Not Active", "Not Active",
+                                          "Not Active"]
+    clk.rows = [(1.0, row(1000)), (2.0, row(2070)), (2.01, row(2060, "Active")), (5.0, row(500))]
+    clk.t0, clk.t1 = 1.9, 2.02
+    s = clk.summary()
+    assert s["window"] == "timed" and s["samples"] == 2 and s["sm_mhz"] == 2065
+    assert s["reasons"] == ["hw_slowdown"]
+    clk.t0, clk.t1 = 3.0, 3.01  # nothing inside: fall back to every sample
+    s = clk.summary()
+    assert s["window"] == "warm-up and timed" and s["samples"] == 4
