@@ -72,13 +72,13 @@ def strip_comments(src):
 
 def kernel_source_hash():
     """SHA-256 over the sources the fixpoint kernel is compiled from, comments
-    stripped."""
+    stripped and whitespace runs collapsed."""
     import hashlib
 
     h = hashlib.sha256()
     for name in ("eg_solve.cu", "eg_device.cuh", "eg_internal.h"):
         with open(os.path.join(ROOT, "paper_1710_03647_gb300", "csrc", name)) as fh:
-            h.update(strip_comments(fh.read()).encode())
+            h.update(" ".join(strip_comments(fh.read()).split()).encode())
     return h.hexdigest()
 
 

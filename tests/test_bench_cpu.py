@@ -23,6 +23,9 @@ def test_comment_edit_keeps_the_hash_code_edit_changes_it():
     h2 = bench.strip_comments("/* reworded */\n" + code)
     assert h1.strip() == h2.strip()
     assert bench.strip_comments(code.replace("= 1", "= 2")) != bench.strip_comments(code)
+    # comment lines leave blank lines behind; the hash collapses whitespace
+    norm = lambda x: " ".join(bench.strip_comments(x).split())
+    assert norm("// a\n// b\n// c\n" + code) == norm(code)
 
 
 def test_traffic_record_names_a_kernel_hash_and_bytes():
