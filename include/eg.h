@@ -154,7 +154,7 @@ eg_status eg_strategy(eg_arena *arena, int32_t credit_bits, int64_t w_scale, int
  * eg_set_option -- per-arena settings of later solves.  None of them changes
  * a result: they change only how fast the least fixpoint is reached.
  *
- *   EG_OPT_LOCAL_WINDOWS (default 256): per-warp budget, per round, of
+ *   EG_OPT_LOCAL_WINDOWS (default 64): per-warp budget, per round, of
  *     32-entry windows worked through the warp's local worklist, which
  *     carries a rise on to the predecessors within the same round; 0 turns
  *     this off (one hop per round, as in Algorithm 3).

@@ -97,7 +97,7 @@ struct eg_arena {
     eg::StateBuffers st32, st64;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evk = nullptr;
     void *host_ctrl = nullptr;  // pinned copy of Ctrl
-    int local_windows = 256;    // per-warp local worklist budget per round (0 disables chaining)
+    int local_windows = 64;     // per-warp local worklist budget per round (0 disables chaining)
     int local_maxdeg = 64;      // largest degree of a vertex handled through the local worklist
     int warm_start = 1;         // TOP on player-1 negative cycles of length <= 2 before lifting
     long long seed_max_pairs = 4096;
@@ -144,7 +144,7 @@ struct Resident {
     void *host_ctrl = nullptr;      // pinned copy of the control block after a slice
     int *host_busy = nullptr;       // pinned copy of busy
     long long r = 0;                // next round
-    int local_windows = 256, local_maxdeg = 64;
+    int local_windows = 64, local_maxdeg = 64;
     long long seed_max_pairs = 4096;
 };
 eg_status resident_create(Resident &R, int device, int cap, int slots, cudaStream_t s);

@@ -1020,11 +1020,15 @@ static eg_status enqueue_solve(const DevArena &A, const WeightView &W, const Ins
     k_init<MULTI, T><<<init_blocks, THREADS, 0, s>>>(a, 0, (int)nf, 0, 0);
     EG_CUDA_TRY(cudaGetLastError());
 
-    int per_sm = 0;
-    EG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fixpoint<MULTI, T>, THREADS, 0));
+    static int per_sm_cache[64] = {0};  // resident blocks per SM, per device
+    int per_sm = device >= 0 && device < 64 ? per_sm_cache[device] : 0;
     if (per_sm < 1) {
-        set_error("fixpoint kernel cannot be resident");
-        return EG_ERR_CUDA;
+        EG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fixpoint<MULTI, T>, THREADS, 0));
+        if (per_sm < 1) {
+            set_error("fixpoint kernel cannot be resident");
+            return EG_ERR_CUDA;
+        }
+        if (device >= 0 && device < 64) per_sm_cache[device] = per_sm;
     }
     dim3 grid(sms * per_sm), block(THREADS);
     void *args[] = {&a};
@@ -1251,6 +1255,30 @@ static eg_status certify(eg_arena *ar, StateBuffers &sb, long long scale, long l
     return EG_OK;
 }
 
+// Queues the copy of the credits of sb to out (host or device): same width,
+// or widened to int64 with TOP mapped when credit_bits == 0.
+static eg_status enqueue_output(eg_arena *ar, StateBuffers &sb, int bits, int credit_bits, void *out,
+                                cudaStream_t s) {
+    const int out_bits = credit_bits == 0 ? 64 : bits;
+    cudaPointerAttributes attr{};
+    const bool dev_out = cudaPointerGetAttributes(&attr, out) == cudaSuccess &&
+                         (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    void *src = sb.d.f;
+    void *tmp = nullptr;
+    if (out_bits != bits) {
+        EG_CUDA_TRY(cudaMallocAsync(&tmp, (size_t)ar->n * 8, s));
+        const int wb = std::min((ar->n + 255) / 256, 4096);
+        k_widen<<<wb, 256, 0, s>>>((const int *)sb.d.f, (long long *)tmp, ar->n);
+        EG_CUDA_TRY(cudaGetLastError());
+        src = tmp;
+    }
+    EG_CUDA_TRY(cudaMemcpyAsync(out, src, (size_t)ar->n * (out_bits / 8),
+                                dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (tmp) EG_CUDA_TRY(cudaFreeAsync(tmp, s));
+    return EG_OK;
+}
+
 eg_status solve(eg_arena *ar, int credit_bits, long long scale, long long shift, void *out, eg_stats *st,
                 cudaStream_t s, long long max_rounds) {
     if (credit_bits != 0 && credit_bits != 32 && credit_bits != 64) {
@@ -1280,16 +1308,27 @@ eg_status solve(eg_arena *ar, int credit_bits, long long scale, long long shift,
     long long nproven = 0;
     // With certification on, a first solve with cap C gets a short round
     // budget; only a game it does not finish goes through the trial caps.
+    bool copied = false;
     if (ar->cap_certify > 0 && ar->warm_start && ar->certify_after > 0 &&
         (max_rounds == 0 || max_rounds > ar->certify_after)) {
+        // the credits are copied out right behind the attempt, before the
+        // host learns whether it finished; the usual case then costs one
+        // synchronisation, and a game that goes on overwrites them later
         Launch L{ar->local_windows, ar->local_maxdeg, 1, ar->seed_max_pairs, ar->certify_after};
-        rc = bits == 32 ? run_phase<int>(ar, sb, WeightView{scale, shift, C}, L, s, tot, dev)
-                        : run_phase<long long>(ar, sb, WeightView{scale, shift, C}, L, s, tot, dev);
+        rc = bits == 32 ? launch_solve<int>(ar, sb, WeightView{scale, shift, C}, s, L)
+                        : launch_solve<long long>(ar, sb, WeightView{scale, shift, C}, s, L);
         if (rc != EG_OK) return rc;
+        if ((rc = enqueue_output(ar, sb, bits, credit_bits, out, s)) != EG_OK) return rc;
+        EG_CUDA_TRY(cudaMemcpyAsync(ar->host_ctrl, sb.d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+        EG_CUDA_TRY(cudaStreamSynchronize(s));
+        add_totals(tot, ar);
+        dev = ((const Ctrl *)ar->host_ctrl)->status;
         if (dev == DEV_OK) {
-            exact = true;
+            exact = copied = true;
         } else if (dev == DEV_BUDGET) {
             dev = DEV_OK;
+            sb.dirty = true;
+        } else {
             sb.dirty = true;
         }
     }
@@ -1308,24 +1347,8 @@ eg_status solve(eg_arena *ar, int credit_bits, long long scale, long long shift,
         if (rc != EG_OK) return rc;
     }
 
-    // credits out: same width, or widened to int64 when credit_bits == 0
-    const int out_bits = credit_bits == 0 ? 64 : bits;
-    cudaPointerAttributes attr{};
-    bool dev_out = cudaPointerGetAttributes(&attr, out) == cudaSuccess &&
-                   (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
-    cudaGetLastError();
-    void *src = sb.d.f;
-    void *tmp = nullptr;
-    if (out_bits != bits) {  // widen int32 -> int64 with TOP mapped
-        EG_CUDA_TRY(cudaMallocAsync(&tmp, (size_t)ar->n * 8, s));
-        const int wb = std::min((ar->n + 255) / 256, 4096);
-        k_widen<<<wb, 256, 0, s>>>((const int *)sb.d.f, (long long *)tmp, ar->n);
-        EG_CUDA_TRY(cudaGetLastError());
-        src = tmp;
-    }
-    EG_CUDA_TRY(cudaMemcpyAsync(out, src, (size_t)ar->n * (out_bits / 8),
-                                dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-    if (tmp) EG_CUDA_TRY(cudaFreeAsync(tmp, s));
+    // credits out (unless the first attempt's copy already holds them)
+    if (!copied && (rc = enqueue_output(ar, sb, bits, credit_bits, out, s)) != EG_OK) return rc;
     if (final_launch)
         EG_CUDA_TRY(cudaMemcpyAsync(ar->host_ctrl, sb.d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     EG_CUDA_TRY(cudaStreamSynchronize(s));
