@@ -546,7 +546,7 @@ def main():
     # 256 mean-payoff threshold queries on the same arena (w' = 256 w - k W,
     # k = -128..127, W = 100): one batched launch vs one solve per query
     thresholds = None
-    if rank == 0 and not args.no_batch:
+    if world == 1 and not args.no_batch:
         ks = list(range(-128, 128))
         plan = eg.Plan(arena.handle, len(ks), part=[0] * len(ks), w_scale=[256] * len(ks),
                        w_shift=[k * 100 for k in ks])
@@ -586,7 +586,7 @@ def main():
 
     # the paper's start (f = 0 everywhere, no warm start), once, for context
     plain = None
-    if rank == 0 and not args.no_plain:
+    if world == 1 and not args.no_plain:
         arena.tune(warm_start=0)
         _, pst = eg.eg_solve_credit(arena.handle, bits, 1, 0, out, stream=stream.cuda_stream)
         arena.tune(warm_start=1)
@@ -597,11 +597,13 @@ def main():
                  "note": "same solver, warm start off (f = 0 start as in the paper)"}
 
     large = batch = served = None
-    if rank == 0 and not args.no_large:
+    # the context sections run once, in single-GPU runs (replica runs time the headline only)
+    single = world == 1
+    if single and not args.no_large:
         large = large_single_game(eg, gen, torch, dev, stream, flush)
-    if rank == 0 and args.batch_games > 0:
+    if single and args.batch_games > 0:
         batch = batch_games(eg, gen, torch, dev, stream, args.batch_games)
-    if rank == 0 and args.serve_requests > 0:
+    if single and args.serve_requests > 0:
         served = serving(eg, gen, torch, dev, stream, args.serve_requests)
 
     if rank != 0:
@@ -614,8 +616,8 @@ def main():
     if os.path.exists(golden):
         g = json.load(open(golden))
         oracle_relax = g["oracle_lift_edge_evals"] + g["oracle_pre_scans"]
-    cpu = None if args.no_cpu_baseline else cpu_baseline()
-    cpu_par = None if args.no_cpu_baseline else cpu_parallel_baseline()
+    cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline()
+    cpu_par = None if args.no_cpu_baseline or world > 1 else cpu_parallel_baseline()
     st0 = stats[-1]
     line = {
         "metric": METRIC, "value": relax_all / (total_ms_max * 1e-3), "unit": UNIT, "n_gpus": world,
