@@ -143,6 +143,7 @@ struct Resident {
     unsigned *bell_dev = nullptr;
     void *host_ctrl = nullptr;      // pinned copy of the control block after a slice
     int *host_busy = nullptr;       // pinned copy of busy
+    long long *host_tab = nullptr;  // pinned staging of the slot tables (scale, shift, C per slot)
     long long r = 0;                // next round
     int local_windows = 64, local_maxdeg = 64;
     long long seed_max_pairs = 4096;

@@ -2051,6 +2051,7 @@ eg_status resident_create(Resident &R, int device, int cap, int slots, cudaStrea
     EG_CUDA_TRY(cudaHostGetDevicePointer((void **)&R.bell_dev, R.bell_host, 0));
     EG_CUDA_TRY(cudaMallocHost(&R.host_ctrl, sizeof(Ctrl)));
     EG_CUDA_TRY(cudaMallocHost((void **)&R.host_busy, (size_t)slots * 4));
+    EG_CUDA_TRY(cudaMallocHost((void **)&R.host_tab, (size_t)slots * 3 * 8));
     return resident_reset(R, s);
 }
 
@@ -2060,6 +2061,8 @@ void resident_free(Resident &R) {
     if (R.bell_host) cudaFreeHost(R.bell_host);
     if (R.host_ctrl) cudaFreeHost(R.host_ctrl);
     if (R.host_busy) cudaFreeHost(R.host_busy);
+    if (R.host_tab) cudaFreeHost(R.host_tab);
+    R.host_tab = nullptr;
     R.block = nullptr;
     R.bell_host = nullptr;
     R.host_ctrl = nullptr;
@@ -2068,7 +2071,12 @@ void resident_free(Resident &R) {
 
 eg_status resident_admit(Resident &R, int slot, int g0, int n, long long scale, long long shift, long long C,
                          cudaStream_t s) {
-    const long long tab[3] = {scale, shift, C};
+    // staged in pinned memory, so the copies stay asynchronous; a slot's entry
+    // is rewritten only after the slot was freed, i.e. after a synchronised slice
+    long long *tab = R.host_tab + 3 * slot;
+    tab[0] = scale;
+    tab[1] = shift;
+    tab[2] = C;
     EG_CUDA_TRY(cudaMemcpyAsync(R.scale + slot, tab + 0, 8, cudaMemcpyHostToDevice, s));
     EG_CUDA_TRY(cudaMemcpyAsync(R.shift + slot, tab + 1, 8, cudaMemcpyHostToDevice, s));
     EG_CUDA_TRY(cudaMemcpyAsync(R.C + slot, tab + 2, 8, cudaMemcpyHostToDevice, s));
@@ -2088,19 +2096,21 @@ eg_status resident_admit(Resident &R, int slot, int g0, int n, long long scale, 
     const int iblocks = (int)std::min<long long>((n + THREADS - 1) / THREADS, (long long)sms * 16);
     k_init<true, long long><<<iblocks, THREADS, 0, s>>>(a, g0, g0 + n, r % 3, r & 1);
     EG_CUDA_TRY(cudaGetLastError());
-    // the host copies tab asynchronously from pageable memory: wait before it goes out of scope
-    EG_CUDA_TRY(cudaStreamSynchronize(s));
     return EG_OK;
 }
 
 eg_status resident_slice(Resident &R, long long rounds, cudaStream_t s, int *dev_status) {
     Args<long long> a = resident_args(R);
     a.max_rounds = rounds > 0 ? R.r + rounds : 0;
-    int per_sm = 0;
-    EG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fixpoint<true, long long>, THREADS, 0));
+    static int per_sm_cache[64] = {0};  // resident blocks per SM, per device
+    int per_sm = R.device >= 0 && R.device < 64 ? per_sm_cache[R.device] : 0;
     if (per_sm < 1) {
-        set_error("fixpoint kernel cannot be resident");
-        return EG_ERR_CUDA;
+        EG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fixpoint<true, long long>, THREADS, 0));
+        if (per_sm < 1) {
+            set_error("fixpoint kernel cannot be resident");
+            return EG_ERR_CUDA;
+        }
+        if (R.device >= 0 && R.device < 64) per_sm_cache[R.device] = per_sm;
     }
     dim3 grid(num_sms(R.device) * per_sm), block(THREADS);
     void *args[] = {&a};
