@@ -132,7 +132,7 @@ int oracle_solve(int64_t n, const int64_t *row_ptr, const int32_t *col, const in
     int64_t head = 0, size = 0; /* FIFO ring of capacity n with set semantics */
 #define PUSH(x) do { if (!in_l[(x)]) { in_l[(x)] = 1; queue[(head + size) % n] = (x); ++size; } } while (0)
 
-    /* lines 1-2: the initial set L */
+    /* the initial set L of Algorithm 1 */
     for (int64_t v = 0; v < n; ++v) {
         int any_neg = 0, all_neg = 1;
         for (int64_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
@@ -144,7 +144,7 @@ int oracle_solve(int64_t n, const int64_t *row_ptr, const int32_t *col, const in
         if (is_p1(owner_bits, v) ? any_neg : all_neg)
             PUSH(v);
     }
-    /* lines 3-6: f = 0 and the player-0 counters */
+    /* f = 0 and the player-0 counters */
     for (int64_t v = 0; v < n; ++v)
         f[v] = 0;
     int64_t recount_evals = 0;
@@ -158,7 +158,7 @@ int oracle_solve(int64_t n, const int64_t *row_ptr, const int32_t *col, const in
 
     int64_t lifts = 0, lift_evals = 0, pre_scans = 0;
     int status = 0;
-    /* lines 7-17 */
+    /* the worklist loop: lift, recount, predecessor filter */
     while (size > 0) {
         if (max_lifts > 0 && lifts >= max_lifts) {
             status = 2;

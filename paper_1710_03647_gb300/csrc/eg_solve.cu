@@ -307,7 +307,8 @@ __global__ void k_seed(Args<T> a, long long max_pairs, unsigned *seed_bits, unsi
 }
 
 // ---------------------------------------------------------------------------
-// Initialisation (Algorithm 3, lines 1-3, with the first lift folded in):
+// Initialisation (Algorithm 3's set-up of f and of the first frontier, with
+// the first lift folded in):
 // f(v) = delta(0, v)(v).  With every successor at 0 that is max(0, -w') taken
 // at the smallest w' of v's edges for a player-1 vertex (max over edges) and
 // at the largest for a player-0 vertex (min over edges), so it needs only the
