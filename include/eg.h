@@ -282,10 +282,13 @@ eg_status eg_solve_credit_noalloc(eg_arena *arena, int32_t credit_bits, int64_t 
  * queue.  A game still unfinished after its arena's EG_OPT_CERTIFY_AFTER
  * rounds (while its EG_OPT_CAP_CERTIFY is on) is taken out and solved alone
  * by eg_solve_credit's certified route; its slot is freed once the resident
- * solve has dropped its remaining work.  The result of every request equals
- * eg_solve_credit on its arena alone (the games are disjoint in the pool;
- * each has its own bound C and weight map), computed in int64.  Do not solve
- * an arena yourself while a request for it is pending.
+ * solve has dropped its remaining work.  A game of at least 2^19 edges fills
+ * the GPU alone and gains nothing from sharing it: it skips the pool and is
+ * solved by eg_solve_credit's route between slices (its stats are that
+ * solve's).  The result of every request equals eg_solve_credit on its arena
+ * alone (the games are disjoint in the pool; each has its own bound C and
+ * weight map).  Results wait in pinned host buffers that the server reuses.
+ * Do not solve an arena yourself while a request for it is pending.
  *
  * eg_poll returns EG_PENDING until the request is done, then copies its
  * credits (n elements: int32 if credit_bits is 32, else int64; host or

@@ -13,7 +13,12 @@
 // the doorbell, so a new request joins the running solve at the next round
 // instead of waiting for the others to finish.  After each slice, a game with
 // no entry left in the round's lists is finished: its credits are copied
-// out, its ranges and slot are freed, and waiting requests take them.
+// by DMA into a pinned result buffer (reused across requests), its ranges and
+// slot are freed, and waiting requests take them.
+//
+// A game of at least SOLO_EDGES edges fills the GPU by itself, so sharing the
+// resident solve gains it nothing: it skips the pool and is solved alone
+// (eg_solve_credit's route) between slices, straight into its result buffer.
 //
 // A game still unfinished after its arena's EG_OPT_CERTIFY_AFTER rounds (with
 // certified trial caps on) is taken out: it is solved alone with the trials
@@ -23,6 +28,7 @@
 #include <cuda_runtime.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -46,7 +52,11 @@ struct Request {
     long long scale = 1, shift = 0;
     bool done = false;
     eg_status status = EG_OK;
-    std::vector<long long> credits;  // int64 with TOP = INT64_MAX
+    // the credits, in a pinned buffer from the server's pool: n elements of
+    // res_w bytes (int32 with TOP = INT32_MAX, or int64 with TOP = INT64_MAX)
+    void *res = nullptr;
+    int res_cls = -1, res_w = 8;
+    size_t res_n = 0;
     eg_stats st{};
     Clock::time_point submitted;
     // placement while resident
@@ -57,6 +67,66 @@ struct Request {
     unsigned long long relax0 = 0, lifts0 = 0, pushes0 = 0, enq0 = 0;
     double dev_ms = 0;
 };
+
+// Pinned host buffers for finished credits, kept by power-of-two size class
+// and reused: results land in them by DMA and stay until eg_poll copies them
+// out, so the worker never copies credits on the host.
+struct PinPool {
+    std::mutex mu;
+    std::vector<std::vector<void *>> free_;  // by class: 2^c bytes
+    std::vector<void *> all;
+    void *get(size_t bytes, int *cls) {
+        int c = 15;
+        while (((size_t)1 << c) < bytes) ++c;
+        *cls = c;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            if ((int)free_.size() > c && !free_[c].empty()) {
+                void *p = free_[c].back();
+                free_[c].pop_back();
+                return p;
+            }
+        }
+        void *p = nullptr;
+        if (cudaMallocHost(&p, (size_t)1 << c) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        std::lock_guard<std::mutex> lk(mu);
+        all.push_back(p);
+        return p;
+    }
+    void put(void *p, int cls) {
+        if (!p) return;
+        std::lock_guard<std::mutex> lk(mu);
+        if ((int)free_.size() <= cls) free_.resize(cls + 1);
+        free_[cls].push_back(p);
+    }
+    void release_all() {
+        for (void *p : all) cudaFreeHost(p);
+        all.clear();
+        free_.clear();
+    }
+};
+
+// Takes a result buffer of n elements of w bytes for r from the pool.
+static eg_status take_result(PinPool &pins, Request *r, size_t n, int w) {
+    r->res = pins.get(std::max<size_t>(n, 1) * w, &r->res_cls);
+    if (!r->res) {
+        set_error("pinned result buffer of %zu bytes failed", n * w);
+        return EG_ERR_OOM;
+    }
+    r->res_n = n;
+    r->res_w = w;
+    return EG_OK;
+}
+
+static void drop_result(PinPool &pins, Request *r) {
+    pins.put(r->res, r->res_cls);
+    r->res = nullptr;
+    r->res_cls = -1;
+    r->res_n = 0;
+}
 
 // First-fit allocator of index ranges, merging freed neighbours.
 struct RangeAlloc {
@@ -98,6 +168,9 @@ struct RangeAlloc {
 constexpr size_t POOL_VERTEX_BYTES = 74;
 constexpr size_t POOL_EDGE_BYTES = 16;
 constexpr long long SLICE_ROUNDS = 32;
+// A game with at least this many edges fills the GPU on its own: it is solved
+// alone (eg_solve_credit's route) between slices instead of joining the pool.
+constexpr long long SOLO_EDGES = 1LL << 19;
 
 __global__ void k_pack_rows(int *dst, const int *src, int n, int add) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dst[i] = src[i] + add;
@@ -156,8 +229,7 @@ struct Server {
     int nactive = 0;
     std::vector<Retiring> retiring;
     Resident R;
-    long long *stage = nullptr;  // pinned staging of finished credits
-    size_t stage_cap = 0;
+    PinPool pins;  // result buffers
 };
 
 static size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -263,13 +335,30 @@ static void complete(Server *S, std::vector<Request *> &fin) {
     fin.clear();
 }
 
+// Solves a large game alone (eg_solve_credit's route, int32 when it fits)
+// straight into its pinned result buffer and completes its request.
+static void solo(Server *S, Request *r, std::vector<Request *> &fin) {
+    const size_t n = (size_t)r->ar->n;
+    const int w = r->credit_bits == 32 ? 4 : 8;
+    eg_stats st{};
+    eg_status rc = take_result(S->pins, r, n, w);
+    if (rc == EG_OK) rc = solve(r->ar, r->credit_bits, r->scale, r->shift, r->res, &st, S->stream, 0);
+    r->status = rc;
+    if (rc == EG_OK)
+        r->st = st;
+    else
+        drop_result(S->pins, r);
+    fin.push_back(r);
+}
+
 // Solves a slow resident game alone with certified trial caps, then retires
 // its slot (views with C < 0: the kernel drops its entries).
 static eg_status take_out(Server *S, Request *r, std::vector<Request *> &fin) {
-    r->credits.resize((size_t)r->ar->n);
     eg_stats st{};
-    eg_status rc = solve(r->ar, 64, r->scale, r->shift, r->credits.data(), &st, S->stream, 0);
+    eg_status rc = take_result(S->pins, r, (size_t)r->ar->n, 8);
+    if (rc == EG_OK) rc = solve(r->ar, 64, r->scale, r->shift, r->res, &st, S->stream, 0);
     r->status = rc;
+    if (rc != EG_OK) drop_result(S->pins, r);
     if (rc == EG_OK) {
         st.credit_bits = r->credit_bits == 32 ? 32 : 64;
         st.rounds += S->R.r - r->r_admit;
@@ -304,13 +393,9 @@ static eg_status harvest(Server *S, std::vector<Request *> &fin) {
         S->retiring.pop_back();
     }
     std::vector<Request *> ready;
-    size_t total = 0;
     for (int k = 0; k < S->max_slots; ++k) {
         Request *r = S->active[k];
-        if (r && !S->R.host_busy[k]) {
-            ready.push_back(r);
-            total += (size_t)r->ar->n;
-        }
+        if (r && !S->R.host_busy[k]) ready.push_back(r);
     }
     // games that are slow in the resident solve go through the certified route
     for (int k = 0; k < S->max_slots; ++k) {
@@ -324,25 +409,15 @@ static eg_status harvest(Server *S, std::vector<Request *> &fin) {
         }
     }
     if (ready.empty()) return EG_OK;
-    if (total > S->stage_cap) {
-        if (S->stage) cudaFreeHost(S->stage);
-        S->stage = nullptr;
-        S->stage_cap = 0;
-        EG_CUDA_TRY(cudaMallocHost((void **)&S->stage, total * 8));
-        S->stage_cap = total;
-    }
-    size_t off = 0;
     for (Request *r : ready) {
-        EG_CUDA_TRY(cudaMemcpyAsync(S->stage + off, (const long long *)S->R.sb.d.f + r->vb, (size_t)r->ar->n * 8,
+        rc = take_result(S->pins, r, (size_t)r->ar->n, 8);
+        if (rc != EG_OK) return rc;
+        EG_CUDA_TRY(cudaMemcpyAsync(r->res, (const long long *)S->R.sb.d.f + r->vb, (size_t)r->ar->n * 8,
                                     cudaMemcpyDeviceToHost, S->stream));
-        off += (size_t)r->ar->n;
     }
     EG_CUDA_TRY(cudaStreamSynchronize(S->stream));
     const Ctrl *hc = (const Ctrl *)S->R.host_ctrl;
-    off = 0;
     for (Request *r : ready) {
-        r->credits.assign(S->stage + off, S->stage + off + r->ar->n);
-        off += (size_t)r->ar->n;
         r->st = eg_stats{};
         r->st.C = r->C;
         r->st.credit_bits = r->credit_bits == 32 ? 32 : 64;
@@ -381,12 +456,12 @@ static void worker_main(Server *S) {
     cudaSetDevice(S->device);
     std::vector<Request *> fin;
     for (;;) {
-        std::vector<Request *> admitted;
+        std::vector<Request *> admitted, alone;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             S->cv.wait(lk, [&] { return S->stop || !S->queue.empty() || S->nactive > 0 || !S->retiring.empty(); });
             if (S->stop) break;
-            while (!S->queue.empty() && !S->free_slots.empty()) {
+            while (!S->queue.empty()) {
                 Request *r = S->queue.front();
                 const long long nv = (long long)r->ar->n + 1, m = r->ar->m;
                 if (nv > S->NV || m > S->NE) {  // can never fit the budget
@@ -395,6 +470,12 @@ static void worker_main(Server *S) {
                     fin.push_back(r);
                     continue;
                 }
+                if (m >= SOLO_EDGES) {  // fills the GPU alone: no slot, solved between slices
+                    S->queue.pop_front();
+                    alone.push_back(r);
+                    continue;
+                }
+                if (S->free_slots.empty()) break;
                 const long long vb = S->vfree.alloc(nv);
                 if (vb < 0) break;
                 const long long eb = S->efree.alloc(m);
@@ -421,6 +502,10 @@ static void worker_main(Server *S) {
                 --S->nactive;
                 fin.push_back(r);
             }
+        }
+        for (Request *r : alone) {
+            solo(S, r, fin);
+            complete(S, fin);
         }
         complete(S, fin);
         if (S->nactive == 0 && S->retiring.empty()) continue;
@@ -565,14 +650,14 @@ eg_status eg_poll(eg_server *S, uint64_t ticket, void *credits_out, eg_stats *st
     }
     eg_status rc = r->status;
     if (rc == EG_OK && credits_out) {
-        const size_t n = r->credits.size();
+        const size_t n = r->res_n;
         std::vector<int32_t> narrow;
-        const void *src = r->credits.data();
-        size_t bytes = n * 8;
-        if (r->credit_bits == 32) {
+        const void *src = r->res;
+        size_t bytes = n * r->res_w;
+        if (r->credit_bits == 32 && r->res_w == 8) {  // int64 state, int32 answer
+            const long long *wide = (const long long *)r->res;
             narrow.resize(n);
-            for (size_t i = 0; i < n; ++i)
-                narrow[i] = r->credits[i] == INT64_MAX ? INT32_MAX : (int32_t)r->credits[i];
+            for (size_t i = 0; i < n; ++i) narrow[i] = wide[i] == INT64_MAX ? INT32_MAX : (int32_t)wide[i];
             src = narrow.data();
             bytes = n * 4;
         }
@@ -593,6 +678,7 @@ eg_status eg_poll(eg_server *S, uint64_t ticket, void *credits_out, eg_stats *st
         eg::set_error("request %llu failed with status %d", (unsigned long long)ticket, rc);
     }
     if (st) *st = r->st;
+    drop_result(S->pins, r);
     delete r;
     return rc;
 }
@@ -613,7 +699,7 @@ eg_status eg_server_destroy(eg_server *S) {
     S->queue.clear();
     eg::resident_free(S->R);
     if (S->pool_block) cudaFree(S->pool_block);
-    if (S->stage) cudaFreeHost(S->stage);
+    S->pins.release_all();
     if (S->stream) cudaStreamDestroy(S->stream);
     if (S->e0) cudaEventDestroy(S->e0);
     if (S->e1) cudaEventDestroy(S->e1);

@@ -198,3 +198,30 @@ def test_slow_games_are_taken_out_to_the_certified_route():
         eg.eg_server_destroy(server)
         for a in arenas:
             a.close()
+
+
+def test_large_games_are_solved_alone_between_slices():
+    # a game of at least 2^19 edges skips the pool and is solved alone between
+    # resident slices; its credits (each width) equal the solve of it alone,
+    # and the small games in the mix are unaffected
+    big = gen.rmat_game(17, 8, seed=4)
+    assert big.m >= 1 << 19
+    smalls = [gen.config(1, 5), gen.rmat_game(12, 8, seed=6), gen.grid_game(24, 24, seed=3)]
+    games = [big] + smalls
+    arenas = [eg.Arena(g) for g in games]
+    server = eg.eg_server_create(4 << 30, 8)
+    try:
+        reqs = []
+        for i, a in enumerate(arenas):
+            for bits, scale, shift in ((0, 1, 0), (32, 1, 0), (64, 4, 7)):
+                reqs.append((i, bits, scale, shift, eg.eg_submit(server, a.handle, bits, scale, shift)))
+        for i, bits, scale, shift, t in reqs:
+            out = np.empty(games[i].n, dtype=np.int32 if bits == 32 else np.int64)
+            rc, st = wait(server, t, out, timeout=120)
+            assert rc == eg.EG_OK, (i, bits, rc, eg.eg_last_error())
+            np.testing.assert_array_equal(out, alone(arenas[i].handle, bits, scale, shift, games[i].n))
+            assert st.ms > 0
+    finally:
+        eg.eg_server_destroy(server)
+        for a in arenas:
+            a.close()
