@@ -336,7 +336,7 @@ def serving(eg, gen, torch, dev, stream, per_rate, scales=(10, 21), seed=11):
     """Poisson arrivals of R-MAT games (scale uniform in [lo, hi], so n is
     log-uniform in [2^lo, 2^hi]; weights in [-100, 100]) served by the
     continuous-batching server vs. one solve at a time in arrival order, at
-    rates 0.5x-4x the serial capacity."""
+    rates 0.25x-4x the serial capacity."""
     import multiprocessing as mp
     import threading
 
@@ -357,7 +357,7 @@ def serving(eg, gen, torch, dev, stream, per_rate, scales=(10, 21), seed=11):
         eg.eg_solve_credit(arenas[k].handle, 0, 1, 0, out, stream=stream.cuda_stream)
     cap = per_rate / (time.perf_counter() - t0)
     rows = []
-    for mult in (0.5, 1.0, 2.0, 4.0):
+    for mult in (0.25, 0.5, 1.0, 2.0, 4.0):
         rate = mult * cap
         gaps = rng.exponential(1.0 / rate, size=per_rate)
         arrive = np.cumsum(gaps)
@@ -450,7 +450,7 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="skip the 4000x4000 grid solve")
     ap.add_argument("--batch-games", type=int, default=4096, help="games in the batched-vs-per-game comparison "
                     "(4096 = the full workload; 0 skips it)")
-    ap.add_argument("--serve-requests", type=int, default=96, help="requests per arrival rate (0 skips serving)")
+    ap.add_argument("--serve-requests", type=int, default=512, help="requests per arrival rate (0 skips serving)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
