@@ -186,9 +186,10 @@ eg_status eg_strategy(eg_arena *arena, int32_t credit_bits, int64_t w_scale, int
  *     trial is exact the solve ends with cap C from the proven TOP starts.
  *     This turns the pseudo-polynomial climb of player-1 vertices to C into
  *     climbs to B.  0 turns it off.  max_rounds bounds each fixpoint launch.
- *   EG_OPT_CERTIFY_AFTER (default 64): with certification on, a plain solve
+ *   EG_OPT_CERTIFY_AFTER (default 8): with certification on, a plain solve
  *     (cap C, warm start) runs first with this round budget, and the trials
  *     start only if it does not reach the fixpoint; 0 starts with the trials.
+ *     The value changes the time to the fixpoint, never the result.
  *
  * EG_ERR_INVALID for an unknown option or a negative value.
  */

@@ -361,6 +361,10 @@ static eg_status create(int64_t n64, int64_t m64, const int64_t *row_ptr, const 
     cudaGetDevice(&a->device);
     a->n = n;
     a->m = m;
+    // EG_OPT_CERTIFY_AFTER's default: 8 plain rounds finish the games that
+    // need no trials (R-MAT, most threshold queries) and hand the others to
+    // the certified trials early; the results do not depend on it
+    a->certify_after = 8;
     eg_status rc = EG_OK;
     char *tmp = nullptr;
 #define TRY(expr)                     \

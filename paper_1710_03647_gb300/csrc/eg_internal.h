@@ -103,7 +103,7 @@ struct eg_arena {
     long long seed_max_pairs = 4096;
     int use_graph = 1;                // batched solves replay a captured graph
     int cap_certify = 4;              // first trial cap of the certified solve, in units of max|w'| (0: off)
-    long long certify_after = 64;     // rounds of a first solve with cap C before the trial caps (0: none)
+    long long certify_after = 64;     // rounds of a first solve with cap C before the trial caps (0: none); eg_create sets the default
     void *cert_block = nullptr;       // device memory of the certified solve:
     unsigned long long *aux = nullptr;  //   counters (4 words)
     unsigned *cert_w0 = nullptr;      //   bitmap of vertices proven won by player 0

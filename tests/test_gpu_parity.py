@@ -448,3 +448,7 @@ def test_cli_solves_and_reports(capsys):
     cli.main(["--workload", "rmat", "--scale", "10", "--local-windows", "0", "--max-rounds", "1"])
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["status"] in (0, eg.EG_ERR_BUDGET) and line["rounds"] <= 1
+    cli.main(["--workload", "batch", "--games", "5", "--repeat", "2"])
+    lines = [json.loads(x) for x in capsys.readouterr().out.strip().splitlines()]
+    assert len(lines) == 2 and all(x["status"] == 0 and x["games"] == 5 for x in lines)
+    assert lines[0]["relaxations"] > 0
