@@ -249,32 +249,11 @@ def large_single_game(eg, gen, torch, dev, stream, flush):
             "C": st["C"], "note": "certified trial caps (default); best of 2 solves"}
 
 
-def _batch_game(args):
-    from paper_1710_03647_gb300 import gen
-
-    i, n, W = args
-    return gen.batch_game(i, n, W)
-
-
-def generate_batch(shapes):
-    """The batch's games from the seeded generator; large batches are made by
-    a pool of spawned processes (spawned, so no CUDA state is forked)."""
-    import multiprocessing as mp
-
-    jobs = [(i, n, W) for i, (n, W) in enumerate(shapes)]
-    workers = min(16, os.cpu_count() or 1)
-    if len(jobs) <= 64 or workers <= 1:
-        return [_batch_game(j) for j in jobs]
-    with mp.get_context("spawn").Pool(workers) as pool:
-        return pool.map(_batch_game, jobs, chunksize=8)
-
-
 def batch_games(eg, gen, torch, dev, stream, count):
     """`count` uneven games (n log-uniform in [1k, 200k], out-degree uniform
     in [2, 16], weights in [-W, W], W log-uniform in [10, 10^4]): all in one
     persistent launch (a plan over one packed arena) vs one solve per game."""
-    shapes = gen.batch_shapes(count)
-    games = generate_batch(shapes)
+    games = gen.batch_games(count)
     n, row_ptr, col, w, owner_bits, part_ptr = eg.pack_games(games)
     h = eg.eg_create(n, int(row_ptr[-1]), row_ptr, col, w, owner_bits=owner_bits)
     eg.eg_set_parts(h, part_ptr)

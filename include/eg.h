@@ -55,6 +55,12 @@ typedef int32_t eg_status;
 typedef struct eg_arena eg_arena;
 typedef struct eg_server eg_server;
 
+#define EG_MAX_PHASES 16
+#define EG_PHASE_ATTEMPT 0     /* lift with cap C under a round budget (or the only lift) */
+#define EG_PHASE_DUAL 1        /* certified trial: lift of the dual game */
+#define EG_PHASE_CAPPED 2      /* certified trial: lift of the game with cap B */
+#define EG_PHASE_FINAL 3       /* lift with cap C from the trials' proven TOP starts */
+
 /* Counters of one solve.  relaxations counts evaluations of f(u) (-) w over
  * edges (pulls of player-0 lifts plus pushes to predecessors); lifts counts
  * player-0 vertices lifted; pushes counts vertices whose rise was sent to
@@ -71,6 +77,17 @@ typedef struct eg_stats {
     int64_t enqueues;
     double ms;             /* device time of initialisation + fixpoint kernels */
     double fixpoint_ms;    /* device time of the persistent fixpoint kernel alone */
+    /* The fixpoint launches of the solve in order, the first EG_MAX_PHASES
+     * of them: a single solve runs a first attempt with cap C and, when that
+     * does not finish, certified trials (a dual lift and a capped lift each,
+     * see EG_OPT_CAP_CERTIFY) and possibly a final lift with cap C. */
+    int32_t phases;        /* launches recorded below */
+    int32_t trials;        /* certified trials run (0: the first attempt finished) */
+    int32_t phase_kind[EG_MAX_PHASES];        /* EG_PHASE_* */
+    int64_t phase_cap[EG_MAX_PHASES];         /* the launch's cap: C, (K + 1) B or B */
+    int64_t phase_rounds[EG_MAX_PHASES];
+    int64_t phase_relaxations[EG_MAX_PHASES];
+    double phase_ms[EG_MAX_PHASES];           /* device time of its fixpoint kernel */
 } eg_stats;
 
 /*
@@ -122,10 +139,15 @@ eg_status eg_bound(eg_arena *arena, int64_t w_scale, int64_t w_shift, int64_t *C
  * credits_out: host or device pointer (detected), caller-owned, n elements.
  * st: optional counters (may be NULL).
  * cuda_stream: the cudaStream_t to run on (NULL = the legacy default stream).
- * max_rounds: round budget (0 = unlimited); EG_ERR_BUDGET when exceeded.
+ * max_rounds: round budget of each fixpoint launch (0 = unlimited);
+ *   EG_ERR_BUDGET when one runs out.
  * Synchronous: returns after the credits are written.  One solve at a time
- * per arena.  EG_ERR_TIMEOUT if a device-side wait gave up; the device
- * stays usable and the arena can be solved again.
+ * per arena.  EG_ERR_TIMEOUT if a device-side wait gave up (see
+ * EG_OPT_WAIT_LIMIT_US); the device stays usable and the arena can be solved
+ * again.  After EG_ERR_BUDGET or EG_ERR_TIMEOUT every credit written is at or
+ * below the least fixpoint: the values a lift with cap C reached before it
+ * stopped, or 0 where the solve stopped inside a certified trial and no such
+ * lift had run.
  */
 eg_status eg_solve_credit(eg_arena *arena, int32_t credit_bits, int64_t w_scale, int64_t w_shift,
                           void *credits_out, eg_stats *st, void *cuda_stream, int64_t max_rounds);
@@ -190,8 +212,19 @@ eg_status eg_strategy(eg_arena *arena, int32_t credit_bits, int64_t w_scale, int
  *     (cap C, warm start) runs first with this round budget, and the trials
  *     start only if it does not reach the fixpoint; 0 starts with the trials.
  *     The value changes the time to the fixpoint, never the result.
+ *   EG_OPT_BLOCKS_PER_SM (default 0): resident blocks per SM of the
+ *     persistent fixpoint kernel; 0 takes as many as fit, a larger value is
+ *     clamped to what fits.  Fewer blocks make the grid barrier cheaper and
+ *     leave fewer lanes in flight.
+ *   EG_OPT_WAIT_LIMIT_US (default 5000000, i.e. 5 s): wall-clock limit of
+ *     each wait of a block at the fixpoint kernel's grid barrier, in
+ *     microseconds (at least 1).  A wait that runs out ends the solve with
+ *     EG_ERR_TIMEOUT; every block leaves the kernel at its next barrier, the
+ *     device stays usable and the arena can be solved again.  A very small
+ *     limit makes ordinary waits run out; that is how the timeout path is
+ *     tested.
  *
- * EG_ERR_INVALID for an unknown option or a negative value.
+ * EG_ERR_INVALID for an unknown option or a value out of range.
  */
 #define EG_OPT_LOCAL_WINDOWS 1
 #define EG_OPT_LOCAL_MAXDEG 2
@@ -200,6 +233,8 @@ eg_status eg_strategy(eg_arena *arena, int32_t credit_bits, int64_t w_scale, int
 #define EG_OPT_GRAPH 5
 #define EG_OPT_CAP_CERTIFY 6
 #define EG_OPT_CERTIFY_AFTER 7
+#define EG_OPT_BLOCKS_PER_SM 8
+#define EG_OPT_WAIT_LIMIT_US 9
 eg_status eg_set_option(eg_arena *arena, int32_t option, int64_t value);
 
 /*
@@ -230,6 +265,9 @@ eg_status eg_set_parts(eg_arena *arena, int32_t parts, const int64_t *part_ptr);
  * credits at element offset i_off (eg_plan_instance) of credits_out (host
  * or device, caller-owned, total elements = sum of the instances' n).
  * Synchronous; one run at a time per plan; the arena must outlive the plan.
+ * max_rounds bounds each fixpoint launch; after EG_ERR_BUDGET or
+ * EG_ERR_TIMEOUT every credit written is at or below its instance's least
+ * fixpoint (0 where the run stopped inside a certified trial).
  */
 typedef struct eg_plan eg_plan;
 eg_status eg_plan_create(eg_arena *arena, int32_t count, const int32_t *part, const int64_t *w_scale,
@@ -245,22 +283,26 @@ eg_status eg_plan_destroy(eg_plan *plan);
  * already handed the GPU's memory to its own caching allocator, or a
  * latency-bound loop where cudaMalloc / cudaFree would synchronise the
  * device and stall other streams.  The paper has no counterpart; it is a
- * deployment variant of the same solve with the same results.
+ * deployment variant of the same solve: the same route (a first attempt with
+ * cap C and the EG_OPT_CERTIFY_AFTER round budget, then certified trial
+ * caps, see EG_OPT_CAP_CERTIFY), the same options and the same results.
  *
  * It allocates nothing: its working memory is one fixed device array inside
- * the library (held by every GPU that loads the library until the process
- * exits), and credits_out -- device memory, n elements of credit_bits (32 or
- * 64 only) -- serves as the credit array while the solve runs.  The arena
- * must have at most EG_NOALLOC_MAX_VERTICES vertices (EG_ERR_INVALID with a
- * message otherwise) and must live on the current device.
+ * the library of about 13.9 MB (held by every GPU that loads the library
+ * until the process exits), and credits_out -- device memory on the arena's
+ * device, n elements of credit_bits (32 or 64 only), aligned to its element
+ * size -- serves as the credit array while the solve runs.  The arena must
+ * have at most EG_NOALLOC_MAX_VERTICES vertices and live on the current
+ * device (EG_ERR_INVALID with a message otherwise, before any work).
  *
- * The first call on a device looks the working array up on that device; make
- * that first call before any stream capture.  All calls share the one array
- * and each call clears what it needs before use, so calls whose work
- * overlaps on the GPU (other threads, or other streams without ordering
- * between them) race and give undefined results: order them.  Synchronous,
- * like eg_solve_credit; on EG_ERR_BUDGET / EG_ERR_TIMEOUT credits_out holds
- * values below the least fixpoint.
+ * The first call on a device (and the first after a device reset) looks the
+ * working array up on that device; make that first call before any stream
+ * capture.  All calls share the one array and each call clears what it needs
+ * before use, so calls whose work overlaps on the GPU (other threads, or
+ * other streams without ordering between them) race and give undefined
+ * results: order them.  Synchronous, like eg_solve_credit; after
+ * EG_ERR_BUDGET / EG_ERR_TIMEOUT every credit in credits_out is at or below
+ * the least fixpoint, as for eg_solve_credit.
  */
 #define EG_NOALLOC_MAX_VERTICES (1 << 18)
 eg_status eg_solve_credit_noalloc(eg_arena *arena, int32_t credit_bits, int64_t w_scale, int64_t w_shift,
@@ -309,6 +351,30 @@ eg_status eg_submit(eg_server *server, eg_arena *arena, int32_t credit_bits, int
                     uint64_t *ticket);
 eg_status eg_poll(eg_server *server, uint64_t ticket, void *credits_out, eg_stats *st);
 eg_status eg_server_destroy(eg_server *server);
+
+/*
+ * eg_server_counters_get -- the server's event counts since it was created:
+ * requests submitted, admitted into the pool, solved alone because they fill
+ * the GPU (solo), taken out of the pool to be solved alone by the certified
+ * route (taken_out), completed (any status), admission attempts refused for
+ * want of pool room (refused; the request stays queued and is retried after
+ * the next slice), and slices of the resident solve run.
+ */
+typedef struct eg_server_counters {
+    int64_t submitted, admitted, solo, taken_out, completed, refused, slices;
+} eg_server_counters;
+eg_status eg_server_counters_get(eg_server *server, eg_server_counters *out);
+
+/*
+ * eg_server_set_option -- settings of a running server.
+ *   EG_SRV_FAIL_RESERVATIONS (test hook, default 0): the next `value`
+ *     reservations of pool room at admission fail as if the pool were full,
+ *     so the refusal and retry path of admission can be exercised on the
+ *     host without exhausting device memory.
+ * EG_ERR_INVALID for an unknown option or a negative value.
+ */
+#define EG_SRV_FAIL_RESERVATIONS 1
+eg_status eg_server_set_option(eg_server *server, int32_t option, int64_t value);
 
 /* eg_last_error -- message of the calling thread's last failure ("" if none). */
 const char *eg_last_error(void);

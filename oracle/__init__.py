@@ -168,3 +168,63 @@ def sweep(n: int, row_ptr, col, w, owner_bits, C: int | None = None, max_sweeps:
     if rc == 2:
         raise OracleError(f"sweep budget of {max_sweeps} exhausted")
     return f[:n], dict(C=C, sweeps=int(st[0]), edge_evals=int(st[1]), threads=int(st[2]))
+
+
+def certified_solve(n: int, row_ptr, col, w, owner_bits, C: int | None = None, cap_mult: int = 4,
+                    trials: int = 8, log=None):
+    """The least EPM by certified trial caps, built from Algorithm 1 alone.
+
+    Two facts, each pinned by brute force in the oracle's tests, let capped
+    runs of Algorithm 1 decide a game whose cap-C run would climb for hours:
+
+      (dual)   in the game with weights -(K w + 1) (K >= 1) and the owners
+               swapped, a vertex whose least fixpoint under any cap is
+               finite is won by player 1 in the original game: player 1
+               then has a positional strategy that keeps every cycle of the
+               play at K w(c) + |c| <= 0, so w(c) < 0 (Lemma "EGcycles");
+      (capped) the least fixpoint under a cap B < C is pointwise at or above
+               the one under C; if every vertex is finite under B or proven
+               lost by (dual), every finite credit is at most B, and a cap
+               at or above the largest finite credit gives the same least
+               fixpoint as C (Sec. 3.1 uses M_G only as an upper bound).
+
+    Trial k runs Algorithm 1 on the dual (K = 8^(k+1), at most n + 1, cap
+    (K + 1) B) and on the game with cap B = cap_mult * max|w| * 4^k, each
+    from f = 0, and stops at the first trial that decides every vertex.
+    If no trial does, the game is solved with cap C.  Each run starts from
+    zero, so the result does not depend on the trial schedule: it is the
+    unique least EPM.  Returns (f, stats) like solve(); stats adds the
+    deciding trial (-1: cap C), its B and K, and the summed work counters.
+    """
+    row_ptr, col, w, owner_bits = _arrays(row_ptr, col, w, owner_bits)
+    if C is None:
+        C = bound(n, row_ptr, w)
+    maxw = max(1, int(np.abs(w).max()) if w.size else 1)
+    dual_owner = np.ascontiguousarray(~owner_bits, dtype=np.uint32)
+    lim = 1 << 61
+    tot = dict(lifts=0, lift_edge_evals=0, pre_scans=0, recount_evals=0)
+
+    def add(st):
+        for k in tot:
+            tot[k] += st[k]
+
+    lost = np.zeros(n, dtype=bool)
+    B, K = cap_mult * maxw, min(8, n + 1)
+    for k in range(trials):
+        if B >= C or K * (maxw + 1) > lim or (K + 1) * B > lim:
+            break
+        wd = -(np.int64(K) * w) - 1
+        fd, st = solve(n, row_ptr, col, wd, dual_owner, C=(K + 1) * B)
+        add(st)
+        lost |= fd != TOP
+        fg, st = solve(n, row_ptr, col, w, owner_bits, C=B)
+        add(st)
+        decided = (fg != TOP) | lost
+        if log:
+            log(f"trial {k}: B={B} K={K} undecided={int((~decided).sum())}")
+        if decided.all():
+            return fg, dict(C=C, trial=k, B=B, K=K, **tot)
+        B, K = B * 4, min(K * 8, n + 1)
+    f, st = solve(n, row_ptr, col, w, owner_bits, C=C)
+    add(st)
+    return f, dict(C=C, trial=-1, B=C, K=0, **tot)

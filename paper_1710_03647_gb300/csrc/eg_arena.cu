@@ -308,6 +308,7 @@ static eg_status destroy(eg_arena *a) {
     if (!a) return EG_OK;
     free_state(a->st32);
     free_state(a->st64);
+    free_state(a->st_dual);
     if (a->block) cudaFree(a->block);
     if (a->cert_block) cudaFree(a->cert_block);
     if (a->ev0) cudaEventDestroy(a->ev0);
@@ -681,6 +682,14 @@ eg_status eg_set_option(eg_arena *arena, int32_t option, int64_t value) {
     case EG_OPT_SEED_MAX_PAIRS: arena->seed_max_pairs = value; break;
     case EG_OPT_CAP_CERTIFY: arena->cap_certify = (int)value; break;
     case EG_OPT_CERTIFY_AFTER: arena->certify_after = value; break;
+    case EG_OPT_BLOCKS_PER_SM: arena->blocks_per_sm = (int)value; break;
+    case EG_OPT_WAIT_LIMIT_US:
+        if (value < 1) {
+            eg::set_error("EG_OPT_WAIT_LIMIT_US takes at least 1");
+            return EG_ERR_INVALID;
+        }
+        arena->wait_limit_ns = (unsigned long long)value * 1000ull;
+        break;
     case EG_OPT_GRAPH:
         if (value > 1) {
             eg::set_error("EG_OPT_GRAPH takes 0 or 1");

@@ -95,6 +95,7 @@ struct eg_arena {
     eg::DevArena d{};
     long long C_plain = -1, wmax_plain = -1;  // bound and max |w| for scale 1, shift 0
     eg::StateBuffers st32, st64;
+    eg::StateBuffers st_dual;  // int64 state of the certified trials' dual lifts
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evk = nullptr;
     void *host_ctrl = nullptr;  // pinned copy of Ctrl
     int local_windows = 64;     // per-warp local worklist budget per round (0 disables chaining)
@@ -104,6 +105,8 @@ struct eg_arena {
     int use_graph = 1;                // batched solves replay a captured graph
     int cap_certify = 4;              // first trial cap of the certified solve, in units of max|w'| (0: off)
     long long certify_after = 64;     // rounds of a first solve with cap C before the trial caps (0: none); eg_create sets the default
+    int blocks_per_sm = 0;            // resident blocks per SM of the fixpoint kernel (0: as many as fit)
+    unsigned long long wait_limit_ns = 5000000000ull;  // limit of each grid-barrier wait
     void *cert_block = nullptr;       // device memory of the certified solve:
     unsigned long long *aux = nullptr;  //   counters (4 words)
     unsigned *cert_w0 = nullptr;      //   bitmap of vertices proven won by player 0

@@ -230,6 +230,8 @@ struct Server {
     std::vector<Retiring> retiring;
     Resident R;
     PinPool pins;  // result buffers
+    long long fail_reservations = 0;  // test hook: reservations still to refuse
+    eg_server_counters ctr{};         // under mu
 };
 
 static size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -329,6 +331,7 @@ static void complete(Server *S, std::vector<Request *> &fin) {
             r->st.status = r->status;
             r->st.ms = std::chrono::duration<double, std::milli>(now - r->submitted).count();
             r->done = true;
+            ++S->ctr.completed;
         }
     }
     S->done_cv.notify_all();
@@ -372,6 +375,10 @@ static eg_status take_out(Server *S, Request *r, std::vector<Request *> &fin) {
     S->active[r->slot] = nullptr;
     r->slot = -1;
     --S->nactive;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        ++S->ctr.taken_out;
+    }
     fin.push_back(r);
     return EG_OK;
 }
@@ -408,13 +415,20 @@ static eg_status harvest(Server *S, std::vector<Request *> &fin) {
             if (rc != EG_OK) return rc;
         }
     }
+    // a game whose pinned result buffer cannot be had now stays resident (it
+    // has no work left) and is collected at a later harvest
+    for (size_t k = 0; k < ready.size();) {
+        if (take_result(S->pins, ready[k], (size_t)ready[k]->ar->n, 8) != EG_OK) {
+            ready[k] = ready.back();
+            ready.pop_back();
+            continue;
+        }
+        ++k;
+    }
     if (ready.empty()) return EG_OK;
-    for (Request *r : ready) {
-        rc = take_result(S->pins, r, (size_t)r->ar->n, 8);
-        if (rc != EG_OK) return rc;
+    for (Request *r : ready)
         EG_CUDA_TRY(cudaMemcpyAsync(r->res, (const long long *)S->R.sb.d.f + r->vb, (size_t)r->ar->n * 8,
                                     cudaMemcpyDeviceToHost, S->stream));
-    }
     EG_CUDA_TRY(cudaStreamSynchronize(S->stream));
     const Ctrl *hc = (const Ctrl *)S->R.host_ctrl;
     for (Request *r : ready) {
@@ -472,15 +486,25 @@ static void worker_main(Server *S) {
                 }
                 if (m >= SOLO_EDGES) {  // fills the GPU alone: no slot, solved between slices
                     S->queue.pop_front();
+                    ++S->ctr.solo;
                     alone.push_back(r);
                     continue;
                 }
                 if (S->free_slots.empty()) break;
+                if (S->fail_reservations > 0) {  // injected: the pool reports no room
+                    --S->fail_reservations;
+                    ++S->ctr.refused;
+                    break;
+                }
                 const long long vb = S->vfree.alloc(nv);
-                if (vb < 0) break;
+                if (vb < 0) {
+                    ++S->ctr.refused;
+                    break;
+                }
                 const long long eb = S->efree.alloc(m);
                 if (eb < 0) {
                     S->vfree.release(vb, nv);
+                    ++S->ctr.refused;
                     break;
                 }
                 S->queue.pop_front();
@@ -490,6 +514,7 @@ static void worker_main(Server *S) {
                 S->free_slots.pop_back();
                 S->active[r->slot] = r;
                 ++S->nactive;
+                ++S->ctr.admitted;
                 admitted.push_back(r);
             }
             *(volatile unsigned *)S->R.bell_host = 0;  // a later eg_submit rings again
@@ -510,6 +535,10 @@ static void worker_main(Server *S) {
         complete(S, fin);
         if (S->nactive == 0 && S->retiring.empty()) continue;
         int dev = DEV_OK;
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            ++S->ctr.slices;
+        }
         cudaEventRecord(S->e0, S->stream);
         eg_status rc = resident_slice(S->R, SLICE_ROUNDS, S->stream, &dev);
         cudaEventRecord(S->e1, S->stream);
@@ -623,6 +652,7 @@ eg_status eg_submit(eg_server *S, eg_arena *arena, int32_t credit_bits, int64_t 
         r->ticket = S->next_ticket++;
         S->all[r->ticket] = r;
         S->queue.push_back(r);
+        ++S->ctr.submitted;
         *ticket = r->ticket;
         if (S->R.bell_host) *(volatile unsigned *)S->R.bell_host = 1;  // end the running slice early
     }
@@ -681,6 +711,35 @@ eg_status eg_poll(eg_server *S, uint64_t ticket, void *credits_out, eg_stats *st
     drop_result(S->pins, r);
     delete r;
     return rc;
+}
+
+eg_status eg_server_set_option(eg_server *S, int32_t option, int64_t value) {
+    eg::clear_error();
+    if (!S || value < 0) {
+        eg::set_error("need a server and a non-negative value");
+        return EG_ERR_INVALID;
+    }
+    switch (option) {
+    case EG_SRV_FAIL_RESERVATIONS: {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->fail_reservations = value;
+        break;
+    }
+    default: eg::set_error("unknown server option %d", option); return EG_ERR_INVALID;
+    }
+    S->cv.notify_one();
+    return EG_OK;
+}
+
+eg_status eg_server_counters_get(eg_server *S, eg_server_counters *out) {
+    eg::clear_error();
+    if (!S || !out) {
+        eg::set_error("server and out are required");
+        return EG_ERR_INVALID;
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    *out = S->ctr;
+    return EG_OK;
 }
 
 eg_status eg_server_destroy(eg_server *S) {

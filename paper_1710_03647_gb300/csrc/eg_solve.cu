@@ -48,11 +48,15 @@
 //                with per-instance certified trials
 //   resident     the resident solve behind the server (eg_server.cu)
 //   noalloc      eg_solve_credit_noalloc over a fixed device array
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <stdint.h>
 #include <stdio.h>
+#include <string.h>
 
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "eg_device.cuh"
 #include "eg_internal.h"
@@ -99,6 +103,8 @@ struct Args {
     unsigned *bits_pull[2];  // dedupe of the pull list of round parity k
     unsigned *bits_push[2];  // dedupe of the push list of round parity k
     const unsigned *seed_bits;  // warm start: vertices that start at TOP (or null)
+    const unsigned *frozen;     // vertices held at 0 and never lifted (or null): proven player-1
+                                // vertices in a dual lift of the certified trials
     unsigned inv;      // 1: owners swapped (the dual game of a certified solve), else 0
     T *acc;
     int *acc_done;
@@ -109,6 +115,7 @@ struct Args {
     const volatile unsigned *doorbell;  // resident solves: host-set flag that ends the slice
     int local_windows;  // per-warp budget of local windows per round (0: no chaining)
     int local_maxdeg;   // largest degree a vertex may have to be chained locally
+    unsigned long long wait_ns;  // limit of each grid-barrier wait
 };
 
 // One instance's view of the arena, carried per list entry.  A negative C
@@ -328,8 +335,11 @@ __global__ void __launch_bounds__(THREADS) k_init(Args<T> a, int g0, int g1, int
             const View vw = view_of<MULTI>(a, g);
             const int v = g - vw.delta;
             const bool p1 = ((__ldg(A.owner_bits + (v >> 5)) >> (v & 31)) & 1u) ^ a.inv;
+            const bool fz = a.frozen && ((__ldg(a.frozen + (g >> 5)) >> (g & 31)) & 1u);
             T f0;
-            if (a.seed_bits && ((a.seed_bits[g >> 5] >> (g & 31)) & 1u)) {
+            if (fz) {
+                f0 = T(0);
+            } else if (a.seed_bits && ((a.seed_bits[g >> 5] >> (g & 31)) & 1u)) {
                 f0 = Cred<T>::TOP;
             } else {
                 const int lo = __ldg(A.wmin + v), hi = __ldg(A.wmax + v);
@@ -339,7 +349,7 @@ __global__ void __launch_bounds__(THREADS) k_init(Args<T> a, int g0, int g1, int
             }
             a.f[g] = f0;
             work = __ldg(A.rrow_ptr + v + 1) - __ldg(A.rrow_ptr + v);
-            want = f0 > T(0) && work > 0;
+            want = !fz && f0 > T(0) && work > 0;
         }
         warp_append(want, (unsigned)g, work, &a.ctrl->push_ctr[slot], a.push_items[buf], a.push_offs[buf]);
     }
@@ -574,8 +584,9 @@ __device__ __forceinline__ void push_edges(const Args<T> &a, int r, int beg, int
             const unsigned pr = __ldg(a.A.rcol + e);
             const int pa = (int)(pr & 0x7fffffffu);
             p = pa + wj.delta;
+            const bool fz = a.frozen && ((__ldg(a.frozen + (p >> 5)) >> (p & 31)) & 1u);
             const T t = ominus<T>(vj, wmapv(__ldg(a.A.rw + e), wj), wj.C);
-            if (t > ld_cg(a.f + p)) {
+            if (!fz && t > ld_cg(a.f + p)) {
                 if (((pr & P1_FLAG) != 0) != (a.inv != 0)) {
                     if (t > atomicMax(a.f + p, t)) {
                         work = __ldg(a.A.rrow_ptr + pa + 1) - __ldg(a.A.rrow_ptr + pa);
@@ -843,12 +854,12 @@ __global__ void __launch_bounds__(THREADS, EG_FIXPOINT_MIN_BLOCKS) k_fixpoint(Ar
                        a.push_offs[r & 1]};
             pull_phase<MULTI, T>(a, r, red, out);
             stage_flush(out);
-            if (!grid_barrier(c, gridDim.x, gen, BARRIER_LIMIT_NS)) break;
+            if (!grid_barrier(c, gridDim.x, gen, a.wait_ns)) break;
         }
         const unsigned long long qc = ld_cg(&c->push_ctr[r % 3]);
         push_phase<MULTI, T>(a, r, red, L);
         if (a.doorbell && blockIdx.x == 0 && threadIdx.x == 0 && *a.doorbell) c->stop_flag = 1;
-        if (!grid_barrier(c, gridDim.x, gen, BARRIER_LIMIT_NS)) break;
+        if (!grid_barrier(c, gridDim.x, gen, a.wait_ns)) break;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             c->rounds += 1;
             c->lifts += pc & 0xffffffffu;
@@ -872,6 +883,19 @@ __global__ void __launch_bounds__(THREADS, EG_FIXPOINT_MIN_BLOCKS) k_fixpoint(Ar
 
 // ---------------------------------------------------------------------------
 // Host side
+
+// A persistent fixpoint kernel waits at grid barriers for all its blocks.
+// Two of them on one device at once can each end up partly resident, the
+// resident blocks of each waiting for blocks that cannot start until the
+// other grid's blocks leave; the barrier's wait limit then ends both with
+// EG_ERR_TIMEOUT.  So within the process the library runs one persistent
+// solve per device at a time: every route that launches the fixpoint kernel
+// holds its device's lock (recursive: routes nest) from before its first
+// launch until its last synchronisation.
+static std::recursive_mutex &persist_lock(int device) {
+    static std::recursive_mutex locks[64];
+    return locks[device >= 0 && device < 64 ? device : 0];
+}
 
 static int num_sms(int device) {
     static int cached[64] = {0};
@@ -915,6 +939,9 @@ eg_status free_state(StateBuffers &sb) {
 }
 
 static size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Blocks of 256 threads for an O(n) pass over n credits.
+static int wblocks_of(long long n, int sms) { return (int)std::min<long long>((n + 255) / 256, (long long)sms * 16); }
 
 // Solve state for nf credits of the given width.
 eg_status alloc_state(StateBuffers &sb, long long nf, int bits) {
@@ -963,7 +990,18 @@ struct Launch {
     long long seed_max_pairs, max_rounds;
     bool preseeded = false;  // seed_bits already holds proven TOP starts (kept; 2-cycle seeds are added)
     unsigned inv = 0;        // 1: owners swapped (dual game)
+    int blocks_per_sm = 0;   // resident blocks per SM of the fixpoint kernel (0: as many as fit)
+    unsigned long long wait_ns = BARRIER_LIMIT_NS;
+    const unsigned *frozen = nullptr;  // vertices held at 0 (dual lifts of the certified trials)
 };
+
+// The arena's launch settings with the given warm start and round budget.
+static Launch launch_of(const eg_arena *ar, int warm_start, long long max_rounds) {
+    Launch L{ar->local_windows, ar->local_maxdeg, warm_start, ar->seed_max_pairs, max_rounds};
+    L.blocks_per_sm = ar->blocks_per_sm;
+    L.wait_ns = ar->wait_limit_ns;
+    return L;
+}
 
 // Enqueues (warm start,) initialisation and the persistent fixpoint on
 // stream s; ev_k (optional) is recorded right before the fixpoint kernel.
@@ -1005,7 +1043,9 @@ static eg_status enqueue_solve(const DevArena &A, const WeightView &W, const Ins
     a.doorbell = nullptr;
     a.local_windows = L.local_windows;
     a.local_maxdeg = L.local_maxdeg;
+    a.wait_ns = L.wait_ns;
     a.inv = L.inv;
+    a.frozen = L.frozen;
     a.seed_bits = nullptr;
     if (L.warm_start || L.preseeded) {
         if (!L.preseeded) EG_CUDA_TRY(cudaMemsetAsync(sb.d.seed_bits, 0, ((size_t)nf + 31) / 32 * 4, s));
@@ -1031,6 +1071,7 @@ static eg_status enqueue_solve(const DevArena &A, const WeightView &W, const Ins
         }
         if (device >= 0 && device < 64) per_sm_cache[device] = per_sm;
     }
+    if (L.blocks_per_sm > 0) per_sm = std::min(per_sm, L.blocks_per_sm);
     dim3 grid(sms * per_sm), block(THREADS);
     void *args[] = {&a};
     if (ev_k) EG_CUDA_TRY(cudaEventRecord(ev_k, s));
@@ -1079,16 +1120,25 @@ __global__ void k_widen(const int *in, long long *out, int n) {
 // the dual's cap costs about cap/L trips: the trials start at K = 8 and a
 // small B and grow both.
 
-// OR of the finite credits into a bitmap (one warp per bitmap word).
+// OR of the finite credits into a bitmap (one warp per bitmap word).  With
+// an instance table that has an `active` array (batched solves), only the
+// credits of active instances count: the others were not computed by the
+// launch just run.
 template <typename T>
-__global__ void k_mark_finite(const T *f, int n, unsigned *bits) {
+__global__ void k_mark_finite(const T *f, int n, unsigned *bits, InstTable I) {
     const int lane = lane_id();
     for (int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < n; base += gridDim.x * blockDim.x) {
         const int g = base + lane;
-        const bool fin = g < n && f[g] != Cred<T>::TOP;
+        bool fin = g < n && f[g] != Cred<T>::TOP;
+        if (fin && I.active) fin = __ldg(I.active + inst_of(I, g)) != 0;
         const unsigned word = __ballot_sync(FULL, fin);
         if (lane == 0 && word) bits[base >> 5] |= word;
     }
+}
+
+// dst |= src over `words` bitmap words.
+__global__ void k_or_bits(unsigned *dst, const unsigned *src, int words) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < words; i += gridDim.x * blockDim.x) dst[i] |= src[i];
 }
 
 // count[0] += credits at TOP that no proof puts in W1; count[1] += proven W1.
@@ -1146,17 +1196,24 @@ __global__ void k_busy_plan(const Ctrl *c, int slot, const int *pull_items, cons
     }
 }
 
-// Counters summed over the fixpoint launches of one solve.
+// Counters summed over the fixpoint launches of one solve, with one record
+// per launch (its kind, cap, rounds, relaxations and kernel time).
+struct PhaseRec {
+    int kind;
+    long long cap, rounds, relax;
+    double kms;
+};
+
 struct Totals {
     long long rounds = 0, lifts = 0, pushes = 0, relax = 0, enqueues = 0, seeded = 0;
     double ms = 0, kms = 0;
+    int trials = 0;
+    std::vector<PhaseRec> phases;
 };
 
-static void add_totals(Totals &t, const eg_arena *ar) {
-    const Ctrl *hc = (const Ctrl *)ar->host_ctrl;
-    float ms = 0.f, kms = 0.f;
-    cudaEventElapsedTime(&ms, ar->ev0, ar->ev1);
-    cudaEventElapsedTime(&kms, ar->evk, ar->ev1);
+// Adds the counters of the launch whose control block was just read back
+// into `hc`; ms and kms are its device times (whole solve, fixpoint kernel).
+static void add_launch(Totals &t, const Ctrl *hc, double ms, double kms, int kind, long long cap) {
     t.rounds += (long long)hc->rounds;
     t.lifts += (long long)hc->lifts;
     t.pushes += (long long)hc->pushes;
@@ -1165,17 +1222,89 @@ static void add_totals(Totals &t, const eg_arena *ar) {
     t.seeded = (long long)hc->seeded;
     t.ms += ms;
     t.kms += kms;
+    t.phases.push_back(PhaseRec{kind, cap, (long long)hc->rounds, (long long)hc->relax, kms});
+}
+
+static void add_totals(Totals &t, const eg_arena *ar, int kind, long long cap) {
+    float ms = 0.f, kms = 0.f;
+    cudaEventElapsedTime(&ms, ar->ev0, ar->ev1);
+    cudaEventElapsedTime(&kms, ar->evk, ar->ev1);
+    add_launch(t, (const Ctrl *)ar->host_ctrl, ms, kms, kind, cap);
+}
+
+static void fill_stats(eg_stats *st, const Totals &t, long long C, long long seeded, int bits, eg_status result) {
+    st->C = C;
+    st->seeded = seeded;
+    st->credit_bits = bits;
+    st->status = result;
+    st->rounds = t.rounds;
+    st->lifts = t.lifts;
+    st->pushes = t.pushes;
+    st->relaxations = t.relax;
+    st->enqueues = t.enqueues;
+    st->ms = t.ms;
+    st->fixpoint_ms = t.kms;
+    st->phases = (int32_t)std::min<size_t>(t.phases.size(), EG_MAX_PHASES);
+    st->trials = t.trials;
+    for (int k = 0; k < EG_MAX_PHASES; ++k) {
+        const bool have = k < st->phases;
+        st->phase_kind[k] = have ? t.phases[k].kind : 0;
+        st->phase_cap[k] = have ? t.phases[k].cap : 0;
+        st->phase_rounds[k] = have ? t.phases[k].rounds : 0;
+        st->phase_relaxations[k] = have ? t.phases[k].relax : 0;
+        st->phase_ms[k] = have ? t.phases[k].kms : 0.0;
+    }
+}
+
+// Where one single-game solve keeps its working memory: the game's state (of
+// the solve's credit width), the int64 state of the dual lifts, and the
+// certified trials' bitmaps of proven player-0 and player-1 vertices with two
+// counters.  eg_solve_credit takes them from the arena and allocates them on
+// first use; eg_solve_credit_noalloc lays them over its fixed device array,
+// where the two states share their lists, bitmaps and scratch (so every
+// launch there resets that scratch first).
+struct SolveMem {
+    StateBuffers *sb = nullptr;
+    StateBuffers *sd = nullptr;
+    unsigned *cert_w0 = nullptr, *cert_w1 = nullptr;
+    unsigned long long *aux = nullptr;
+    bool fixed = false;     // laid over the allocation-free array
+    bool in_place = false;  // sb's credit array is the caller's output buffer
+};
+
+// The dual state and the trial bitmaps of an allocating solve.
+static eg_status cert_memory(eg_arena *ar, SolveMem &m) {
+    if (m.fixed) return EG_OK;
+    // the dual lifts get their own state: the capped fixpoint of the game
+    // stays in m.sb while the dual runs
+    eg_status rc = alloc_state(ar->st_dual, ar->n, 64);
+    if (rc != EG_OK) return rc;
+    m.sd = &ar->st_dual;
+    if (!ar->cert_block) {
+        const size_t words = ((size_t)ar->n + 31) / 32, bm = align_up(words * 4);
+        char *blk = nullptr;
+        EG_CUDA_TRY(cudaMalloc((void **)&blk, 256 + 2 * bm));
+        ar->cert_block = blk;
+        ar->aux = (unsigned long long *)blk;
+        ar->cert_w0 = (unsigned *)(blk + 256);
+        ar->cert_w1 = (unsigned *)(blk + 256 + bm);
+    }
+    m.cert_w0 = ar->cert_w0;
+    m.cert_w1 = ar->cert_w1;
+    m.aux = ar->aux;
+    return EG_OK;
 }
 
 // One solve run to its end on s; adds its counters and returns its device status.
 template <typename T>
-static eg_status run_phase(eg_arena *ar, StateBuffers &sb, const WeightView &W, const Launch &L, cudaStream_t s,
-                           Totals &t, int &dev) {
+static eg_status run_phase(eg_arena *ar, const SolveMem &m, StateBuffers &sb, const WeightView &W, const Launch &L,
+                           cudaStream_t s, Totals &t, int kind, int &dev) {
+    if (m.fixed) sb.dirty = true;  // the scratch is shared with the other state
     eg_status rc = launch_solve<T>(ar, sb, W, s, L);
     if (rc != EG_OK) return rc;
     EG_CUDA_TRY(cudaMemcpyAsync(ar->host_ctrl, sb.d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     EG_CUDA_TRY(cudaStreamSynchronize(s));
-    add_totals(t, ar);
+    add_totals(t, ar, kind, W.C);
     dev = ((const Ctrl *)ar->host_ctrl)->status;
     if (dev != DEV_OK) sb.dirty = true;
     return EG_OK;
@@ -1184,12 +1313,20 @@ static eg_status run_phase(eg_arena *ar, StateBuffers &sb, const WeightView &W, 
 constexpr int CERT_TRIALS = 6;
 
 // Trials k = 0..5 with B = cap_certify * max|w'| * 4^k and K = 8^(k+1) (at
-// most n + 1).  exact: sb holds the least fixpoint.  seeded: sb's seed bitmap
-// holds proven TOP starts for a final solve with cap C.
+// most n + 1).  A trial first lifts the game with cap B from the proven
+// player-1 vertices at TOP; its finite vertices are proven player-0 wins.
+// If every vertex is then finite or proven lost, that capped fixpoint is
+// the least one.  Otherwise the dual is lifted with the proven player-0
+// vertices at TOP and the proven player-1 vertices frozen at 0 (sinks of the
+// dual: a vertex that is finite there is lost by player 0, because player 1
+// either keeps the play on negative cycles or reaches a vertex already
+// proven lost), and the count is taken again over the same capped fixpoint.
+// exact: m.sb holds the least fixpoint.  seeded: m.cert_w1 holds proven TOP
+// starts for a final solve with cap C.
 template <typename T>
-static eg_status certify(eg_arena *ar, StateBuffers &sb, long long scale, long long shift, long long C,
-                         long long wmax, cudaStream_t s, long long max_rounds, Totals &t, int &dev, bool &exact,
-                         bool &seeded, long long &nproven) {
+static eg_status certify(eg_arena *ar, SolveMem &m, long long scale, long long shift, long long C, long long wmax,
+                         cudaStream_t s, long long max_rounds, Totals &t, int &dev, bool &exact, bool &seeded,
+                         long long &nproven) {
     exact = seeded = false;
     dev = DEV_OK;
     if (ar->cap_certify <= 0 || !ar->warm_start) return EG_OK;
@@ -1201,50 +1338,60 @@ static eg_status certify(eg_arena *ar, StateBuffers &sb, long long scale, long l
     if (wmax > LIM / 4 / ar->cap_certify) return EG_OK;
     long long B = (long long)ar->cap_certify * std::max(1LL, wmax);
     if (B >= C) return EG_OK;
-    eg_status rc = ensure_state(ar, 64);
+    eg_status rc = cert_memory(ar, m);
     if (rc != EG_OK) return rc;
-    const size_t words = ((size_t)n + 31) / 32, bm = (words * 4 + 255) & ~size_t(255);
-    if (!ar->cert_block) {
-        char *blk = nullptr;
-        EG_CUDA_TRY(cudaMalloc((void **)&blk, 256 + 2 * bm));
-        ar->cert_block = blk;
-        ar->aux = (unsigned long long *)blk;
-        ar->cert_w0 = (unsigned *)(blk + 256);
-        ar->cert_w1 = (unsigned *)(blk + 256 + bm);
-    }
-    EG_CUDA_TRY(cudaMemsetAsync(ar->cert_w0, 0, 2 * bm, s));
-    StateBuffers &sd = ar->st64;
+    StateBuffers &sb = *m.sb, &sd = *m.sd;
+    const size_t words = ((size_t)n + 31) / 32;
+    EG_CUDA_TRY(cudaMemsetAsync(m.cert_w0, 0, words * 4, s));
+    EG_CUDA_TRY(cudaMemsetAsync(m.cert_w1, 0, words * 4, s));
     const int sms = num_sms(ar->device);
     const int wblocks = (int)std::min<long long>((n + 255) / 256, (long long)sms * 16);
+    const InstTable all{};
+    unsigned long long *h = (unsigned long long *)ar->host_ctrl;
+    // h[0] = credits of sb at TOP without a proof of loss, h[1] = proven losses
+    auto count = [&]() -> eg_status {
+        EG_CUDA_TRY(cudaMemsetAsync(m.aux, 0, 2 * sizeof(unsigned long long), s));
+        k_count_undecided<T><<<wblocks, 256, 0, s>>>((const T *)sb.d.f, m.cert_w1, (int)n, m.aux);
+        EG_CUDA_TRY(cudaGetLastError());
+        EG_CUDA_TRY(cudaMemcpyAsync(h, m.aux, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        EG_CUDA_TRY(cudaStreamSynchronize(s));
+        nproven = (long long)h[1];
+        return EG_OK;
+    };
     long long K = std::min(8LL, n + 1);
     for (int k = 0; k < CERT_TRIALS && B < C; ++k) {
         if (K > LIM / inner || B > LIM / (K + 1)) break;
-        // dual: proven player-0 vertices start at TOP
-        EG_CUDA_TRY(cudaMemcpyAsync(sd.d.seed_bits, ar->cert_w0, words * 4, cudaMemcpyDeviceToDevice, s));
-        Launch Ld{ar->local_windows, ar->local_maxdeg, 1, ar->seed_max_pairs, max_rounds};
+        t.trials = k + 1;
+        // the game with cap B: proven player-1 vertices start at TOP
+        EG_CUDA_TRY(cudaMemcpyAsync(sb.d.seed_bits, m.cert_w1, words * 4, cudaMemcpyDeviceToDevice, s));
+        Launch Lp = launch_of(ar, 1, max_rounds);
+        Lp.preseeded = true;
+        rc = run_phase<T>(ar, m, sb, WeightView{scale, shift, B}, Lp, s, t, EG_PHASE_CAPPED, dev);
+        if (rc != EG_OK || dev != DEV_OK) return rc;
+        seeded = true;
+        // the warm start's own finds are proven losses too
+        k_or_bits<<<(int)std::min<size_t>((words + 255) / 256, 1024), 256, 0, s>>>(m.cert_w1, sb.d.seed_bits,
+                                                                                   (int)words);
+        k_mark_finite<T><<<wblocks, 256, 0, s>>>((const T *)sb.d.f, (int)n, m.cert_w0, all);
+        EG_CUDA_TRY(cudaGetLastError());
+        if ((rc = count()) != EG_OK) return rc;
+        if (h[0] == 0) {
+            exact = true;
+            return EG_OK;
+        }
+        // the dual: proven player-0 vertices start at TOP, proven player-1
+        // vertices are held at 0
+        EG_CUDA_TRY(cudaMemcpyAsync(sd.d.seed_bits, m.cert_w0, words * 4, cudaMemcpyDeviceToDevice, s));
+        Launch Ld = launch_of(ar, 1, max_rounds);
         Ld.inv = 1;
         Ld.preseeded = true;
+        Ld.frozen = m.cert_w1;
         const WeightView Wd{-K * scale, 1 - K * shift, (K + 1) * B};
-        rc = run_phase<long long>(ar, sd, Wd, Ld, s, t, dev);
+        rc = run_phase<long long>(ar, m, sd, Wd, Ld, s, t, EG_PHASE_DUAL, dev);
         if (rc != EG_OK || dev != DEV_OK) return rc;
-        k_mark_finite<long long><<<wblocks, 256, 0, s>>>((const long long *)sd.d.f, (int)n, ar->cert_w1);
+        k_mark_finite<long long><<<wblocks, 256, 0, s>>>((const long long *)sd.d.f, (int)n, m.cert_w1, all);
         EG_CUDA_TRY(cudaGetLastError());
-        // the game: proven player-1 vertices start at TOP
-        EG_CUDA_TRY(cudaMemcpyAsync(sb.d.seed_bits, ar->cert_w1, words * 4, cudaMemcpyDeviceToDevice, s));
-        Launch Lp{ar->local_windows, ar->local_maxdeg, 1, ar->seed_max_pairs, max_rounds};
-        Lp.preseeded = true;
-        rc = run_phase<T>(ar, sb, WeightView{scale, shift, B}, Lp, s, t, dev);
-        if (rc != EG_OK || dev != DEV_OK) return rc;
-        EG_CUDA_TRY(cudaMemsetAsync(ar->aux, 0, 2 * sizeof(unsigned long long), s));
-        k_count_undecided<T><<<wblocks, 256, 0, s>>>((const T *)sb.d.f, sb.d.seed_bits, (int)n, ar->aux);
-        EG_CUDA_TRY(cudaGetLastError());
-        k_mark_finite<T><<<wblocks, 256, 0, s>>>((const T *)sb.d.f, (int)n, ar->cert_w0);
-        EG_CUDA_TRY(cudaGetLastError());
-        unsigned long long h[2] = {0, 0};
-        EG_CUDA_TRY(cudaMemcpyAsync(h, ar->aux, sizeof(h), cudaMemcpyDeviceToHost, s));
-        EG_CUDA_TRY(cudaStreamSynchronize(s));
-        seeded = true;
-        nproven = (long long)h[1];
+        if ((rc = count()) != EG_OK) return rc;
         if (h[0] == 0) {
             exact = true;
             return EG_OK;
@@ -1280,6 +1427,110 @@ static eg_status enqueue_output(eg_arena *ar, StateBuffers &sb, int bits, int cr
     return EG_OK;
 }
 
+// The route of one single-game solve, in the memory m gives it: a first
+// lift with cap C under a short round budget; if it does not finish, the
+// certified trials; if they decide nothing, a final lift with cap C from
+// their proven TOP starts.  bits is the width of m.sb; unless m.in_place,
+// the credits are then copied to out (widened when credit_bits is 0).
+static eg_status solve_route(eg_arena *ar, SolveMem &m, int bits, int credit_bits, long long scale, long long shift,
+                             long long C, long long wmax, void *out, eg_stats *st, cudaStream_t s,
+                             long long max_rounds) {
+    std::lock_guard<std::recursive_mutex> one_persistent_solve(persist_lock(ar->device));
+    StateBuffers &sb = *m.sb;
+    eg_status rc = EG_OK;
+    Totals tot;
+    int dev = DEV_OK;
+    bool exact = false, seeded = false;
+    long long nproven = 0;
+    // With certification on, a first solve with cap C gets a short round
+    // budget; only a game it does not finish goes through the trial caps.
+    bool copied = m.in_place, attempt_out = false;
+    if (ar->cap_certify > 0 && ar->warm_start && ar->certify_after > 0 &&
+        (max_rounds == 0 || max_rounds > ar->certify_after)) {
+        // the credits are copied out right behind the attempt, before the
+        // host learns whether it finished; the usual case then costs one
+        // synchronisation, and a game that goes on overwrites them later
+        if (m.fixed) sb.dirty = true;
+        const Launch L = launch_of(ar, 1, ar->certify_after);
+        rc = bits == 32 ? launch_solve<int>(ar, sb, WeightView{scale, shift, C}, s, L)
+                        : launch_solve<long long>(ar, sb, WeightView{scale, shift, C}, s, L);
+        if (rc != EG_OK) return rc;
+        if (!m.in_place) {
+            if ((rc = enqueue_output(ar, sb, bits, credit_bits, out, s)) != EG_OK) return rc;
+            attempt_out = true;
+        }
+        EG_CUDA_TRY(cudaMemcpyAsync(ar->host_ctrl, sb.d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+        EG_CUDA_TRY(cudaStreamSynchronize(s));
+        add_totals(tot, ar, EG_PHASE_ATTEMPT, C);
+        dev = ((const Ctrl *)ar->host_ctrl)->status;
+        if (dev == DEV_OK) {
+            exact = copied = true;
+        } else {
+            sb.dirty = true;
+            if (dev == DEV_BUDGET) dev = DEV_OK;
+        }
+    }
+    bool trial_failed = false;
+    if (!exact && dev == DEV_OK) {
+        rc = bits == 32 ? certify<int>(ar, m, scale, shift, C, wmax, s, max_rounds, tot, dev, exact, seeded, nproven)
+                        : certify<long long>(ar, m, scale, shift, C, wmax, s, max_rounds, tot, dev, exact, seeded,
+                                             nproven);
+        if (rc != EG_OK) return rc;
+        trial_failed = dev != DEV_OK;
+    }
+    const bool final_launch = dev == DEV_OK && !exact;
+    if (final_launch) {
+        if (m.fixed) sb.dirty = true;
+        Launch L = launch_of(ar, ar->warm_start, max_rounds);
+        L.preseeded = seeded;  // proven losses start at TOP
+        if (seeded)
+            EG_CUDA_TRY(cudaMemcpyAsync(sb.d.seed_bits, m.cert_w1, ((size_t)ar->n + 31) / 32 * 4,
+                                        cudaMemcpyDeviceToDevice, s));
+        WeightView W{scale, shift, C};
+        rc = bits == 32 ? launch_solve<int>(ar, sb, W, s, L) : launch_solve<long long>(ar, sb, W, s, L);
+        if (rc != EG_OK) return rc;
+    }
+
+    // credits out (unless the first attempt's copy already holds them).  A
+    // lift with cap C stopped early is below the least fixpoint everywhere;
+    // a dual or capped lift stopped early bounds nothing, so then the output
+    // keeps the first attempt's credits, or else becomes all zeros.
+    bool zero_host = false;
+    if (trial_failed) {
+        if (m.in_place || !attempt_out) {
+            const size_t bytes = (size_t)ar->n * ((credit_bits == 0 ? 64 : bits) / 8);
+            cudaPointerAttributes attr{};
+            const bool dev_out = cudaPointerGetAttributes(&attr, out) == cudaSuccess &&
+                                 (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
+            cudaGetLastError();
+            if (dev_out) EG_CUDA_TRY(cudaMemsetAsync(out, 0, bytes, s));
+            else zero_host = true;
+        }
+    } else if (!copied && (rc = enqueue_output(ar, sb, bits, credit_bits, out, s)) != EG_OK) {
+        return rc;
+    }
+    if (final_launch)
+        EG_CUDA_TRY(cudaMemcpyAsync(ar->host_ctrl, sb.d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    EG_CUDA_TRY(cudaStreamSynchronize(s));
+    if (zero_host) memset(out, 0, (size_t)ar->n * ((credit_bits == 0 ? 64 : bits) / 8));
+    if (final_launch) {
+        add_totals(tot, ar, tot.phases.empty() ? EG_PHASE_ATTEMPT : EG_PHASE_FINAL, C);
+        dev = ((const Ctrl *)ar->host_ctrl)->status;
+    }
+    eg_status result = EG_OK;
+    if (dev == DEV_TIMEOUT) {
+        set_error("a device-side wait exceeded its limit");
+        result = EG_ERR_TIMEOUT;
+        sb.dirty = true;
+    } else if (dev == DEV_BUDGET) {
+        set_error("round budget of %lld exhausted", max_rounds);
+        result = EG_ERR_BUDGET;
+        sb.dirty = true;
+    }
+    if (st) fill_stats(st, tot, C, seeded ? nproven : tot.seeded, bits, result);
+    return result;
+}
+
 eg_status solve(eg_arena *ar, int credit_bits, long long scale, long long shift, void *out, eg_stats *st,
                 cudaStream_t s, long long max_rounds) {
     if (credit_bits != 0 && credit_bits != 32 && credit_bits != 64) {
@@ -1301,86 +1552,9 @@ eg_status solve(eg_arena *ar, int credit_bits, long long scale, long long shift,
         return EG_ERR_OVERFLOW;
     }
     if ((rc = ensure_state(ar, bits)) != EG_OK) return rc;
-    StateBuffers &sb = bits == 32 ? ar->st32 : ar->st64;
-
-    Totals tot;
-    int dev = DEV_OK;
-    bool exact = false, seeded = false;
-    long long nproven = 0;
-    // With certification on, a first solve with cap C gets a short round
-    // budget; only a game it does not finish goes through the trial caps.
-    bool copied = false;
-    if (ar->cap_certify > 0 && ar->warm_start && ar->certify_after > 0 &&
-        (max_rounds == 0 || max_rounds > ar->certify_after)) {
-        // the credits are copied out right behind the attempt, before the
-        // host learns whether it finished; the usual case then costs one
-        // synchronisation, and a game that goes on overwrites them later
-        Launch L{ar->local_windows, ar->local_maxdeg, 1, ar->seed_max_pairs, ar->certify_after};
-        rc = bits == 32 ? launch_solve<int>(ar, sb, WeightView{scale, shift, C}, s, L)
-                        : launch_solve<long long>(ar, sb, WeightView{scale, shift, C}, s, L);
-        if (rc != EG_OK) return rc;
-        if ((rc = enqueue_output(ar, sb, bits, credit_bits, out, s)) != EG_OK) return rc;
-        EG_CUDA_TRY(cudaMemcpyAsync(ar->host_ctrl, sb.d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-        EG_CUDA_TRY(cudaStreamSynchronize(s));
-        add_totals(tot, ar);
-        dev = ((const Ctrl *)ar->host_ctrl)->status;
-        if (dev == DEV_OK) {
-            exact = copied = true;
-        } else if (dev == DEV_BUDGET) {
-            dev = DEV_OK;
-            sb.dirty = true;
-        } else {
-            sb.dirty = true;
-        }
-    }
-    if (!exact && dev == DEV_OK) {
-        rc = bits == 32 ? certify<int>(ar, sb, scale, shift, C, wmax, s, max_rounds, tot, dev, exact, seeded, nproven)
-                        : certify<long long>(ar, sb, scale, shift, C, wmax, s, max_rounds, tot, dev, exact, seeded,
-                                             nproven);
-        if (rc != EG_OK) return rc;
-    }
-    const bool final_launch = dev == DEV_OK && !exact;
-    if (final_launch) {
-        Launch L{ar->local_windows, ar->local_maxdeg, ar->warm_start, ar->seed_max_pairs, max_rounds};
-        L.preseeded = seeded;
-        WeightView W{scale, shift, C};
-        rc = bits == 32 ? launch_solve<int>(ar, sb, W, s, L) : launch_solve<long long>(ar, sb, W, s, L);
-        if (rc != EG_OK) return rc;
-    }
-
-    // credits out (unless the first attempt's copy already holds them)
-    if (!copied && (rc = enqueue_output(ar, sb, bits, credit_bits, out, s)) != EG_OK) return rc;
-    if (final_launch)
-        EG_CUDA_TRY(cudaMemcpyAsync(ar->host_ctrl, sb.d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-    EG_CUDA_TRY(cudaStreamSynchronize(s));
-    if (final_launch) {
-        add_totals(tot, ar);
-        dev = ((const Ctrl *)ar->host_ctrl)->status;
-    }
-    eg_status result = EG_OK;
-    if (dev == DEV_TIMEOUT) {
-        set_error("a device-side wait exceeded its limit");
-        result = EG_ERR_TIMEOUT;
-        sb.dirty = true;
-    } else if (dev == DEV_BUDGET) {
-        set_error("round budget of %lld exhausted", max_rounds);
-        result = EG_ERR_BUDGET;
-        sb.dirty = true;
-    }
-    if (st) {
-        st->C = C;
-        st->seeded = seeded ? nproven : tot.seeded;
-        st->credit_bits = bits;
-        st->status = result;
-        st->rounds = tot.rounds;
-        st->lifts = tot.lifts;
-        st->pushes = tot.pushes;
-        st->relaxations = tot.relax;
-        st->enqueues = tot.enqueues;
-        st->ms = tot.ms;
-        st->fixpoint_ms = tot.kms;
-    }
-    return result;
+    SolveMem m;
+    m.sb = bits == 32 ? &ar->st32 : &ar->st64;
+    return solve_route(ar, m, bits, credit_bits, scale, shift, C, wmax, out, st, s, max_rounds);
 }
 
 }  // namespace eg
@@ -1409,8 +1583,9 @@ struct eg_plan_impl {
     void *host_ctrl = nullptr;
     cudaGraphExec_t graph = nullptr;
     long long graph_rounds = -1;
-    int graph_opts[3] = {-1, -1, -1};
+    int graph_opts[4] = {-1, -1, -1, -1};
     long long graph_pairs = -1;
+    unsigned long long graph_wait = 0;
     bool graph_failed = false;
     // certified trial caps (allocated on first use)
     std::vector<long long> wmax;  // max |w'| per instance
@@ -1586,42 +1761,37 @@ void plan_instance_info(const eg_plan_impl *p, int i, long long *offset, long lo
     if (bits) *bits = p->bits_alone[i];
 }
 
-static void plan_add_totals(Totals &t, const eg_plan_impl *p, bool kernel_event) {
-    const Ctrl *hc = (const Ctrl *)p->host_ctrl;
+// Counters of the plan's last launch; a graph replay has no event right
+// before its fixpoint kernel, so its kernel time is the whole replay's.  The
+// caps differ per instance: the phase records carry 0.
+static void plan_add_totals(Totals &t, const eg_plan_impl *p, bool kernel_event, int kind) {
     float ms = 0.f, kms = 0.f;
     cudaEventElapsedTime(&ms, p->ev0, p->ev1);
     if (kernel_event) cudaEventElapsedTime(&kms, p->evk, p->ev1);
-    t.rounds += (long long)hc->rounds;
-    t.lifts += (long long)hc->lifts;
-    t.pushes += (long long)hc->pushes;
-    t.relax += (long long)hc->relax;
-    t.enqueues += (long long)hc->enqueues;
-    t.seeded = (long long)hc->seeded;
-    t.ms += ms;
-    t.kms += kernel_event ? kms : ms;
+    add_launch(t, (const Ctrl *)p->host_ctrl, ms, kernel_event ? kms : ms, kind, 0);
 }
 
 // One batched solve over the instances of I (direct launches), run to its end.
 template <typename T>
 static eg_status plan_phase(eg_plan_impl *p, StateBuffers &sb, const InstTable &I, const Launch &L, cudaStream_t s,
-                            Totals &t, int &dev) {
+                            Totals &t, int kind, int &dev) {
     EG_CUDA_TRY(cudaEventRecord(p->ev0, s));
     eg_status rc = enqueue_solve<true, T>(p->ar->d, WeightView{1, 0, 0}, I, p->nf, sb, L, p->ar->device, s, p->evk);
     if (rc != EG_OK) return rc;
     EG_CUDA_TRY(cudaEventRecord(p->ev1, s));
     EG_CUDA_TRY(cudaMemcpyAsync(p->host_ctrl, sb.d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
     EG_CUDA_TRY(cudaStreamSynchronize(s));
-    plan_add_totals(t, p, true);
+    plan_add_totals(t, p, true, kind);
     dev = ((const Ctrl *)p->host_ctrl)->status;
     if (dev != DEV_OK) sb.dirty = true;
     return EG_OK;
 }
 
-// Certified trial caps per instance (readings of the single solve's trials):
-// instances the budgeted first attempt finished are exact; every other one
-// runs dual and capped lifts with its own B and K until it is decided, and
-// is then left as it is by the later launches.  What no trial decides ends
-// with cap C from its proven TOP starts.
+// Certified trial caps per instance (the single solve's trials, per
+// instance): instances the budgeted first attempt finished are exact; every
+// other one runs capped and dual lifts with its own B and K until it is
+// decided, and is then left as it is by the later launches.  What no trial
+// decides ends with cap C from its proven TOP starts.
 template <typename T>
 static eg_status plan_certify(eg_plan_impl *p, cudaStream_t s, long long max_rounds, Totals &t, int &dev) {
     eg_arena *ar = p->ar;
@@ -1667,7 +1837,7 @@ static eg_status plan_certify(eg_plan_impl *p, cudaStream_t s, long long max_rou
     constexpr long long LIM = 1LL << 61;
     const long long raw = std::max(1LL, ar->wmax_plain), mult = ar->cap_certify;
     std::vector<long long> B(cnt, 0), K(cnt, 0), hs(cnt), hh(cnt), hC(cnt);
-    std::vector<int> direct(cnt, 0), skip(cnt, 0), on(cnt, 0);
+    std::vector<int> direct(cnt, 0), skip(cnt, 0), on(cnt, 0), dual_on(cnt, 0);
     std::vector<unsigned long long> und(cnt);
     auto fits = [&](int i) {
         const long long inner = (p->scale[i] < 0 ? -p->scale[i] : p->scale[i]) * raw +
@@ -1699,41 +1869,28 @@ static eg_status plan_certify(eg_plan_impl *p, cudaStream_t s, long long max_rou
         EG_CUDA_TRY(cudaStreamSynchronize(s));  // the host vectors change before the next upload
         return EG_OK;
     };
-    const int wblocks = (int)std::min<long long>((nf + 255) / 256, (long long)sms * 16);
+    // und[i] = credits of instance i at TOP in the capped fixpoint without a proof of loss
+    auto count = [&]() -> eg_status {
+        EG_CUDA_TRY(cudaMemsetAsync(p->d_cnt, 0, (size_t)cnt * 8, s));
+        k_count_undecided_inst<T><<<wblocks_of(nf, sms), 256, 0, s>>>((const T *)p->sb.d.f, p->cert_w1, p->I,
+                                                                      (int)nf, p->d_cnt);
+        EG_CUDA_TRY(cudaGetLastError());
+        EG_CUDA_TRY(cudaMemcpyAsync(und.data(), p->d_cnt, (size_t)cnt * 8, cudaMemcpyDeviceToHost, s));
+        EG_CUDA_TRY(cudaStreamSynchronize(s));
+        return EG_OK;
+    };
+    const int wblocks = wblocks_of(nf, sms);
     eg_status rc = EG_OK;
     for (int k = 0; k < CERT_TRIALS; ++k) {
-        int ntrial = 0, ndual = 0;
+        int ntrial = 0;
         for (int i = 0; i < cnt; ++i) {
             on[i] = act[i] && !skip[i];
             ntrial += on[i];
         }
         if (ntrial == 0) break;
-        // dual lifts: owners swapped, weights -(K w' + 1), cap (K + 1) B
-        std::vector<int> dual_on(cnt, 0);
-        for (int i = 0; i < cnt; ++i) {
-            hs[i] = p->scale[i];
-            hh[i] = p->shift[i];
-            hC[i] = p->C[i];
-            if (on[i] && !direct[i]) {
-                dual_on[i] = 1;
-                ++ndual;
-                hs[i] = -K[i] * p->scale[i];
-                hh[i] = 1 - K[i] * p->shift[i];
-                hC[i] = (K[i] + 1) * B[i];
-            }
-        }
-        if (ndual > 0) {
-            if ((rc = upload(dual_on)) != EG_OK) return rc;
-            EG_CUDA_TRY(cudaMemcpyAsync(p->sd.d.seed_bits, p->cert_w0, words * 4, cudaMemcpyDeviceToDevice, s));
-            Launch Ld{ar->local_windows, ar->local_maxdeg, 1, ar->seed_max_pairs, max_rounds};
-            Ld.inv = 1;
-            Ld.preseeded = true;
-            rc = plan_phase<long long>(p, p->sd, It, Ld, s, t, dev);
-            if (rc != EG_OK || dev != DEV_OK) return rc;
-            k_mark_finite<long long><<<wblocks, 256, 0, s>>>((const long long *)p->sd.d.f, (int)nf, p->cert_w1);
-            EG_CUDA_TRY(cudaGetLastError());
-        }
-        // the game's lifts with cap B (cap C for the direct ones)
+        t.trials = k + 1;
+        // the game's lifts with cap B (cap C for the direct ones): proven
+        // player-1 vertices start at TOP
         for (int i = 0; i < cnt; ++i) {
             hs[i] = p->scale[i];
             hh[i] = p->shift[i];
@@ -1741,23 +1898,50 @@ static eg_status plan_certify(eg_plan_impl *p, cudaStream_t s, long long max_rou
         }
         if ((rc = upload(on)) != EG_OK) return rc;
         EG_CUDA_TRY(cudaMemcpyAsync(p->sb.d.seed_bits, p->cert_w1, words * 4, cudaMemcpyDeviceToDevice, s));
-        Launch Lp{ar->local_windows, ar->local_maxdeg, 1, ar->seed_max_pairs, max_rounds};
+        Launch Lp = launch_of(ar, 1, max_rounds);
         Lp.preseeded = true;
-        rc = plan_phase<T>(p, p->sb, It, Lp, s, t, dev);
+        rc = plan_phase<T>(p, p->sb, It, Lp, s, t, EG_PHASE_CAPPED, dev);
         if (rc != EG_OK || dev != DEV_OK) return rc;
-        EG_CUDA_TRY(cudaMemsetAsync(p->d_cnt, 0, (size_t)cnt * 8, s));
-        k_count_undecided_inst<T><<<wblocks, 256, 0, s>>>((const T *)p->sb.d.f, p->sb.d.seed_bits, It, (int)nf,
-                                                         p->d_cnt);
-        k_mark_finite<T><<<wblocks, 256, 0, s>>>((const T *)p->sb.d.f, (int)nf, p->cert_w0);
+        k_or_bits<<<(int)std::min<size_t>((words + 255) / 256, 1024), 256, 0, s>>>(p->cert_w1, p->sb.d.seed_bits,
+                                                                                   (int)words);
+        k_mark_finite<T><<<wblocks, 256, 0, s>>>((const T *)p->sb.d.f, (int)nf, p->cert_w0, It);
         EG_CUDA_TRY(cudaGetLastError());
-        EG_CUDA_TRY(cudaMemcpyAsync(und.data(), p->d_cnt, (size_t)cnt * 8, cudaMemcpyDeviceToHost, s));
-        EG_CUDA_TRY(cudaStreamSynchronize(s));
+        if ((rc = count()) != EG_OK) return rc;
+        int ndual = 0;
         for (int i = 0; i < cnt; ++i) {
+            dual_on[i] = 0;
             if (!on[i]) continue;
             if (direct[i] || und[i] == 0) {
                 act[i] = 0;  // exact: later launches leave it as it is
                 continue;
             }
+            dual_on[i] = 1;
+            ++ndual;
+        }
+        if (ndual > 0) {
+            // dual lifts: owners swapped, weights -(K w' + 1), cap (K + 1) B;
+            // proven player-0 vertices start at TOP, proven player-1 ones are held at 0
+            for (int i = 0; i < cnt; ++i) {
+                hs[i] = dual_on[i] ? -K[i] * p->scale[i] : p->scale[i];
+                hh[i] = dual_on[i] ? 1 - K[i] * p->shift[i] : p->shift[i];
+                hC[i] = dual_on[i] ? (K[i] + 1) * B[i] : p->C[i];
+            }
+            if ((rc = upload(dual_on)) != EG_OK) return rc;
+            EG_CUDA_TRY(cudaMemcpyAsync(p->sd.d.seed_bits, p->cert_w0, words * 4, cudaMemcpyDeviceToDevice, s));
+            Launch Ld = launch_of(ar, 1, max_rounds);
+            Ld.inv = 1;
+            Ld.preseeded = true;
+            Ld.frozen = p->cert_w1;
+            rc = plan_phase<long long>(p, p->sd, It, Ld, s, t, EG_PHASE_DUAL, dev);
+            if (rc != EG_OK || dev != DEV_OK) return rc;
+            k_mark_finite<long long><<<wblocks, 256, 0, s>>>((const long long *)p->sd.d.f, (int)nf, p->cert_w1, It);
+            EG_CUDA_TRY(cudaGetLastError());
+            if ((rc = count()) != EG_OK) return rc;
+            for (int i = 0; i < cnt; ++i)
+                if (dual_on[i] && und[i] == 0) act[i] = 0;  // the capped fixpoint is exact
+        }
+        for (int i = 0; i < cnt; ++i) {
+            if (!on[i] || !act[i]) continue;
             if (B[i] > LIM / 4) {
                 skip[i] = 1;
                 continue;
@@ -1779,19 +1963,19 @@ static eg_status plan_certify(eg_plan_impl *p, cudaStream_t s, long long max_rou
     }
     if ((rc = upload(act)) != EG_OK) return rc;
     EG_CUDA_TRY(cudaMemcpyAsync(p->sb.d.seed_bits, p->cert_w1, words * 4, cudaMemcpyDeviceToDevice, s));
-    Launch Lf{ar->local_windows, ar->local_maxdeg, 1, ar->seed_max_pairs, max_rounds};
+    Launch Lf = launch_of(ar, 1, max_rounds);
     Lf.preseeded = true;
-    return plan_phase<T>(p, p->sb, It, Lf, s, t, dev);
+    return plan_phase<T>(p, p->sb, It, Lf, s, t, EG_PHASE_FINAL, dev);
 }
 
 eg_status plan_run(eg_plan_impl *p, void *out, eg_stats *st, cudaStream_t user, long long max_rounds) {
     eg_arena *ar = p->ar;
+    std::lock_guard<std::recursive_mutex> one_persistent_solve(persist_lock(ar->device));
     // with certification on, the first batched solve gets a short round
     // budget, and only the instances it does not finish go through the trials
     const bool cert = ar->cap_certify > 0 && ar->warm_start && ar->certify_after > 0 &&
                       (max_rounds == 0 || max_rounds > ar->certify_after);
-    const Launch L{ar->local_windows, ar->local_maxdeg, ar->warm_start, ar->seed_max_pairs,
-                   cert ? ar->certify_after : max_rounds};
+    const Launch L = launch_of(ar, ar->warm_start, cert ? ar->certify_after : max_rounds);
     cudaStream_t s = user ? user : p->own;
     // scratch left dirty by an aborted run is reset outside the graph
     if (p->sb.dirty) {
@@ -1807,7 +1991,8 @@ eg_status plan_run(eg_plan_impl *p, void *out, eg_stats *st, cudaStream_t user, 
     }
     const bool same = p->graph && p->graph_rounds == L.max_rounds && p->graph_opts[0] == L.local_windows &&
                       p->graph_opts[1] == L.local_maxdeg && p->graph_opts[2] == L.warm_start &&
-                      p->graph_pairs == L.seed_max_pairs;
+                      p->graph_opts[3] == L.blocks_per_sm && p->graph_pairs == L.seed_max_pairs &&
+                      p->graph_wait == L.wait_ns;
     if (!ar->use_graph && p->graph) {
         cudaGraphExecDestroy(p->graph);
         p->graph = nullptr;
@@ -1831,7 +2016,9 @@ eg_status plan_run(eg_plan_impl *p, void *out, eg_stats *st, cudaStream_t user, 
             p->graph_opts[0] = L.local_windows;
             p->graph_opts[1] = L.local_maxdeg;
             p->graph_opts[2] = L.warm_start;
+            p->graph_opts[3] = L.blocks_per_sm;
             p->graph_pairs = L.seed_max_pairs;
+            p->graph_wait = L.wait_ns;
         } else {
             p->graph = nullptr;
             p->graph_failed = true;  // capture unsupported here: launch directly from now on
@@ -1849,7 +2036,7 @@ eg_status plan_run(eg_plan_impl *p, void *out, eg_stats *st, cudaStream_t user, 
     int dev = DEV_OK;
     if (cert) {
         EG_CUDA_TRY(cudaStreamSynchronize(s));
-        plan_add_totals(tot, p, p->graph == nullptr);
+        plan_add_totals(tot, p, p->graph == nullptr, EG_PHASE_ATTEMPT);
         dev = ((const Ctrl *)p->host_ctrl)->status;
         if (dev == DEV_BUDGET) {
             eg_status rc = p->bits == 32 ? plan_certify<int>(p, s, max_rounds, tot, dev)
@@ -1857,25 +2044,35 @@ eg_status plan_run(eg_plan_impl *p, void *out, eg_stats *st, cudaStream_t user, 
             if (rc != EG_OK) return rc;
         }
     }
-    // credits out
+    // credits out; a dual or capped lift stopped early bounds nothing from
+    // below, so then the output is all zeros (below every fixpoint)
     cudaPointerAttributes attr{};
     const bool dev_out = cudaPointerGetAttributes(&attr, out) == cudaSuccess &&
                          (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
     cudaGetLastError();
+    const bool trial_failed = cert && dev != DEV_OK && !tot.phases.empty() &&
+                              (tot.phases.back().kind == EG_PHASE_DUAL || tot.phases.back().kind == EG_PHASE_CAPPED);
+    const size_t out_bytes = (size_t)p->nf * (p->out_bits / 8);
+    if (trial_failed) {
+        if (dev_out) EG_CUDA_TRY(cudaMemsetAsync(out, 0, out_bytes, s));
+        EG_CUDA_TRY(cudaStreamSynchronize(s));
+        if (!dev_out) memset(out, 0, out_bytes);
+    }
     void *src = p->sb.d.f, *tmp = nullptr;
-    if (p->out_bits != p->bits) {
+    if (!trial_failed && p->out_bits != p->bits) {
         EG_CUDA_TRY(cudaMallocAsync(&tmp, (size_t)p->nf * 8, s));
         k_widen<<<(int)std::min<long long>((p->nf + 255) / 256, 4096), 256, 0, s>>>((const int *)p->sb.d.f,
                                                                                     (long long *)tmp, (int)p->nf);
         EG_CUDA_TRY(cudaGetLastError());
         src = tmp;
     }
-    EG_CUDA_TRY(cudaMemcpyAsync(out, src, (size_t)p->nf * (p->out_bits / 8),
-                                dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    if (!trial_failed)
+        EG_CUDA_TRY(cudaMemcpyAsync(out, src, out_bytes, dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                    s));
     if (tmp) EG_CUDA_TRY(cudaFreeAsync(tmp, s));
     EG_CUDA_TRY(cudaStreamSynchronize(s));
     if (!cert) {
-        plan_add_totals(tot, p, p->graph == nullptr);
+        plan_add_totals(tot, p, p->graph == nullptr, EG_PHASE_ATTEMPT);
         dev = ((const Ctrl *)p->host_ctrl)->status;
     }
     eg_status result = EG_OK;
@@ -1891,17 +2088,8 @@ eg_status plan_run(eg_plan_impl *p, void *out, eg_stats *st, cudaStream_t user, 
     if (st) {
         long long cmax = 0;
         for (long long c : p->C) cmax = std::max(cmax, c);
-        st->C = cmax;
-        st->seeded = (int64_t)tot.seeded;
-        st->credit_bits = p->bits;
-        st->status = result;
-        st->rounds = (int64_t)tot.rounds;
-        st->lifts = (int64_t)tot.lifts;
-        st->pushes = (int64_t)tot.pushes;
-        st->relaxations = (int64_t)tot.relax;
-        st->enqueues = (int64_t)tot.enqueues;
-        st->ms = tot.ms;
-        st->fixpoint_ms = p->graph ? -1.0 : tot.kms;
+        fill_stats(st, tot, cmax, tot.seeded, p->bits, result);
+        if (p->graph) st->fixpoint_ms = -1.0;
     }
     return result;
 }
@@ -1997,6 +2185,7 @@ static Args<long long> resident_args(const Resident &R) {
         a.bits_push[k] = R.sb.d.bits_push[k];
     }
     a.seed_bits = R.sb.d.seed_bits;
+    a.frozen = nullptr;
     a.inv = 0;
     a.acc = (long long *)R.sb.d.acc;
     a.acc_done = R.sb.d.acc_done;
@@ -2007,6 +2196,7 @@ static Args<long long> resident_args(const Resident &R) {
     a.doorbell = R.bell_dev;
     a.local_windows = R.local_windows;
     a.local_maxdeg = R.local_maxdeg;
+    a.wait_ns = BARRIER_LIMIT_NS;
     return a;
 }
 
@@ -2101,6 +2291,7 @@ eg_status resident_admit(Resident &R, int slot, int g0, int n, long long scale, 
 }
 
 eg_status resident_slice(Resident &R, long long rounds, cudaStream_t s, int *dev_status) {
+    std::lock_guard<std::recursive_mutex> one_persistent_solve(persist_lock(R.device));
     Args<long long> a = resident_args(R);
     a.max_rounds = rounds > 0 ? R.r + rounds : 0;
     static int per_sm_cache[64] = {0};  // resident blocks per SM, per device
@@ -2145,32 +2336,75 @@ eg_status resident_busy(Resident &R, cudaStream_t s) {
 // allocator, or a latency-bound loop where a cudaMalloc / cudaFree would
 // synchronise the device and stall every other stream.  For them the solver
 // keeps its working memory (lists, dedupe bitmaps, partial minima, control
-// block) in one file-scope device array of fixed size, and it writes credits
-// straight into the caller's device output buffer, which doubles as the
-// credit array of the solve.  Every GPU that loads the library holds this
-// array until the process exits; every call reuses it.
+// block, the certified trials' bitmaps and the credits of their dual lifts)
+// in one file-scope device array of fixed size, and it computes the credits
+// straight in the caller's device output buffer.  Every GPU that loads the
+// library holds this array until the process exits; every call reuses it.
+// The solve takes the same route as eg_solve_credit (a first attempt with a
+// short round budget, then certified trial caps), so it gives the same
+// credits in about the same time.
 
 namespace eg {
 
 constexpr long long NOALLOC_MAX_N = EG_NOALLOC_MAX_VERTICES;
 constexpr size_t NOALLOC_WORDS = (size_t)(NOALLOC_MAX_N + 31) / 32;
 constexpr size_t noalloc_up(size_t x) { return (x + 255) & ~size_t(255); }
-// layout: 8 lists of n ints, 5 bitmaps, n partial minima (int64), n counts,
-// control block, two 64-bit bound accumulators
+// layout: 8 lists of n ints, 7 bitmaps (5 of the solve state, the proven
+// player-0 and player-1 vertices), n partial minima (int64), n counts, the
+// int64 credits of the dual lifts, control block, 4 counters (bound
+// accumulators, trial counts)
 constexpr size_t NA_LISTS = 0;
 constexpr size_t NA_BITS = NA_LISTS + 8 * noalloc_up((size_t)NOALLOC_MAX_N * 4);
-constexpr size_t NA_ACC = NA_BITS + 5 * noalloc_up(NOALLOC_WORDS * 4);
+constexpr size_t NA_ACC = NA_BITS + 7 * noalloc_up(NOALLOC_WORDS * 4);
 constexpr size_t NA_DONE = NA_ACC + noalloc_up((size_t)NOALLOC_MAX_N * 8);
-constexpr size_t NA_CTRL = NA_DONE + noalloc_up((size_t)NOALLOC_MAX_N * 4);
-constexpr size_t NA_BOUND = NA_CTRL + noalloc_up(sizeof(Ctrl));
-constexpr size_t NA_BYTES = NA_BOUND + 256;
+constexpr size_t NA_DUAL = NA_DONE + noalloc_up((size_t)NOALLOC_MAX_N * 4);
+constexpr size_t NA_CTRL = NA_DUAL + noalloc_up((size_t)NOALLOC_MAX_N * 8);
+constexpr size_t NA_COUNT = NA_CTRL + noalloc_up(sizeof(Ctrl));
+constexpr size_t NA_BYTES = NA_COUNT + 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NA_BYTES];
 
-// Device address of g_noalloc_scratch on each device, looked up once per
-// device (with that device current) on the first call made there.
-static void *g_noalloc_addr[64];
+// Device address of g_noalloc_scratch, looked up (cudaGetSymbolAddress, with
+// the device current) once per device and context: in host code the array's
+// name is a host-side stand-in, never a device address.  The cache is keyed
+// on the id of the current context, so a device reset or another context on
+// the device gets a fresh lookup; where that id cannot be had, every call
+// looks the address up.
+struct ScratchAddr {
+    unsigned long long ctx_id;
+    void *addr;
+};
+static ScratchAddr g_noalloc_addr[64];
 static std::mutex g_noalloc_mu;
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Id of the calling thread's current context (0 if unknown); called under
+// g_noalloc_mu.
+static unsigned long long current_ctx_id() {
+    static CtxGetCurrentFn get_cur = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool resolved = false;
+    if (!resolved) {
+        resolved = true;
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void **)&get_cur, 12000, cudaEnableDefault, &q1) !=
+                cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess)
+            get_cur = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", (void **)&get_id, 12000, cudaEnableDefault, &q2) !=
+                cudaSuccess ||
+            q2 != cudaDriverEntryPointSuccess)
+            get_id = nullptr;
+        cudaGetLastError();
+    }
+    if (!get_cur || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_cur(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 static eg_status noalloc_scratch(int device, unsigned char **out) {
     if (device < 0 || device >= 64) {
@@ -2178,16 +2412,19 @@ static eg_status noalloc_scratch(int device, unsigned char **out) {
         return EG_ERR_INVALID;
     }
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[device]) {
+    const unsigned long long id = current_ctx_id();
+    ScratchAddr &c = g_noalloc_addr[device];
+    if (id == 0 || c.ctx_id != id || !c.addr) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
             set_error("cudaGetSymbolAddress of the solver scratch failed: %s", cudaGetErrorString(e));
             return EG_ERR_CUDA;
         }
-        g_noalloc_addr[device] = p;
+        c.ctx_id = id;
+        c.addr = p;
     }
-    *out = (unsigned char *)g_noalloc_addr[device];
+    *out = (unsigned char *)c.addr;
     return EG_OK;
 }
 
@@ -2206,6 +2443,13 @@ static eg_status solve_noalloc(eg_arena *ar, int credit_bits, long long scale, l
         set_error("weight map out of range");
         return EG_ERR_INVALID;
     }
+    int device = 0;
+    EG_CUDA_TRY(cudaGetDevice(&device));
+    if (device != ar->device) {
+        set_error("the arena lives on device %d, the current device is %d", ar->device, device);
+        return EG_ERR_INVALID;
+    }
+    // the kernels write credits straight through credits_out
     cudaPointerAttributes attr{};
     if (cudaPointerGetAttributes(&attr, out) != cudaSuccess ||
         (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)) {
@@ -2213,10 +2457,12 @@ static eg_status solve_noalloc(eg_arena *ar, int credit_bits, long long scale, l
         set_error("credits_out must be device memory (it holds the credits during the solve)");
         return EG_ERR_INVALID;
     }
-    int device = 0;
-    EG_CUDA_TRY(cudaGetDevice(&device));
-    if (device != ar->device) {
-        set_error("the arena lives on device %d, the current device is %d", ar->device, device);
+    if (attr.type == cudaMemoryTypeDevice && attr.device != ar->device) {
+        set_error("credits_out lives on device %d, the arena on device %d", attr.device, ar->device);
+        return EG_ERR_INVALID;
+    }
+    if ((uintptr_t)out % (uintptr_t)(credit_bits / 8) != 0) {
+        set_error("credits_out must be aligned to %d bytes", credit_bits / 8);
         return EG_ERR_INVALID;
     }
     unsigned char *base = nullptr;
@@ -2224,11 +2470,11 @@ static eg_status solve_noalloc(eg_arena *ar, int credit_bits, long long scale, l
     if (rc != EG_OK) return rc;
 
     // bound C of the weight view, accumulated in the scratch
-    unsigned long long *dbound = (unsigned long long *)(base + NA_BOUND);
-    EG_CUDA_TRY(cudaMemsetAsync(dbound, 0, 16, s));
-    k_bound<<<num_sms(device) * 8, 256, 0, s>>>(ar->d, WeightView{scale, shift, 0}, dbound, dbound + 1);
+    unsigned long long *dcount = (unsigned long long *)(base + NA_COUNT);
+    EG_CUDA_TRY(cudaMemsetAsync(dcount, 0, 16, s));
+    k_bound<<<num_sms(device) * 8, 256, 0, s>>>(ar->d, WeightView{scale, shift, 0}, dcount, dcount + 1);
     EG_CUDA_TRY(cudaGetLastError());
-    EG_CUDA_TRY(cudaMemcpyAsync(ar->host_ctrl, dbound, 16, cudaMemcpyDeviceToHost, s));
+    EG_CUDA_TRY(cudaMemcpyAsync(ar->host_ctrl, dcount, 16, cudaMemcpyDeviceToHost, s));
     EG_CUDA_TRY(cudaStreamSynchronize(s));
     const long long C = (long long)((unsigned long long *)ar->host_ctrl)[0];
     const long long wmax = (long long)((unsigned long long *)ar->host_ctrl)[1];
@@ -2236,13 +2482,19 @@ static eg_status solve_noalloc(eg_arena *ar, int credit_bits, long long scale, l
         set_error("int32 credits cannot hold C + max|w'| = %lld", C + wmax);
         return EG_ERR_OVERFLOW;
     }
+    if (scale == 1 && shift == 0) {
+        ar->C_plain = C;
+        ar->wmax_plain = wmax;
+    }
 
-    // solve state laid over the scratch; the output buffer is the credit array
+    // the game's state laid over the scratch, with the output buffer as its
+    // credit array; the dual lifts' state shares its lists, bitmaps, partial
+    // minima and control block and has its own int64 credits
     const size_t n = (size_t)ar->n, words = (n + 31) / 32;
-    StateBuffers sb;
+    StateBuffers sb, sd;
     sb.bits = credit_bits;
     sb.nf = ar->n;
-    sb.dirty = true;  // every call starts from cleared scratch
+    sb.dirty = true;
     sb.d.f = out;
     for (int k = 0; k < 2; ++k) {
         sb.d.pull_items[k] = (int *)(base + NA_LISTS + (4 * k + 0) * noalloc_up(n * 4));
@@ -2256,43 +2508,19 @@ static eg_status solve_noalloc(eg_arena *ar, int credit_bits, long long scale, l
     sb.d.acc = base + NA_ACC;
     sb.d.acc_done = (int *)(base + NA_DONE);
     sb.d.ctrl = (Ctrl *)(base + NA_CTRL);
+    sd = sb;
+    sd.bits = 64;
+    sd.d.f = base + NA_DUAL;
 
-    const WeightView W{scale, shift, C};
-    const Launch L{ar->local_windows, ar->local_maxdeg, ar->warm_start, ar->seed_max_pairs, max_rounds};
-    InstTable none{1, 0, nullptr, nullptr, nullptr, nullptr, nullptr};
-    EG_CUDA_TRY(cudaEventRecord(ar->ev0, s));
-    rc = credit_bits == 32 ? enqueue_solve<false, int>(ar->d, W, none, ar->n, sb, L, device, s, ar->evk)
-                           : enqueue_solve<false, long long>(ar->d, W, none, ar->n, sb, L, device, s, ar->evk);
-    if (rc != EG_OK) return rc;
-    EG_CUDA_TRY(cudaEventRecord(ar->ev1, s));
-    EG_CUDA_TRY(cudaMemcpyAsync(ar->host_ctrl, sb.d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
-    EG_CUDA_TRY(cudaStreamSynchronize(s));
-    const Ctrl *hc = (const Ctrl *)ar->host_ctrl;
-    float ms = 0.f, kms = 0.f;
-    cudaEventElapsedTime(&ms, ar->ev0, ar->ev1);
-    cudaEventElapsedTime(&kms, ar->evk, ar->ev1);
-    eg_status result = EG_OK;
-    if (hc->status == DEV_TIMEOUT) {
-        set_error("a device-side wait exceeded its limit");
-        result = EG_ERR_TIMEOUT;
-    } else if (hc->status == DEV_BUDGET) {
-        set_error("round budget of %lld exhausted", max_rounds);
-        result = EG_ERR_BUDGET;
-    }
-    if (st) {
-        st->C = C;
-        st->seeded = (int64_t)hc->seeded;
-        st->credit_bits = credit_bits;
-        st->status = result;
-        st->rounds = (int64_t)hc->rounds;
-        st->lifts = (int64_t)hc->lifts;
-        st->pushes = (int64_t)hc->pushes;
-        st->relaxations = (int64_t)hc->relax;
-        st->enqueues = (int64_t)hc->enqueues;
-        st->ms = ms;
-        st->fixpoint_ms = kms;
-    }
-    return result;
+    SolveMem m;
+    m.sb = &sb;
+    m.sd = &sd;
+    m.cert_w0 = (unsigned *)(base + NA_BITS + 5 * noalloc_up(words * 4));
+    m.cert_w1 = (unsigned *)(base + NA_BITS + 6 * noalloc_up(words * 4));
+    m.aux = dcount + 2;
+    m.fixed = true;
+    m.in_place = true;
+    return solve_route(ar, m, credit_bits, credit_bits, scale, shift, C, wmax, out, st, s, max_rounds);
 }
 
 }  // namespace eg

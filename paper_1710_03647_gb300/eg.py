@@ -36,14 +36,45 @@ STATUS_NAMES = {0: "EG_OK", 1: "EG_PENDING", -1: "EG_ERR_INVALID", -2: "EG_ERR_N
                 -7: "EG_ERR_BUDGET", -8: "EG_ERR_BUSY"}
 
 
+EG_MAX_PHASES = 16
+EG_PHASE_ATTEMPT = 0
+EG_PHASE_DUAL = 1
+EG_PHASE_CAPPED = 2
+EG_PHASE_FINAL = 3
+PHASE_NAMES = {0: "attempt", 1: "dual", 2: "capped", 3: "final"}
+
+
 class eg_stats(ctypes.Structure):
     _fields_ = [("C", ctypes.c_int64), ("seeded", ctypes.c_int64), ("credit_bits", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("rounds", ctypes.c_int64), ("lifts", ctypes.c_int64), ("pushes", ctypes.c_int64),
                 ("relaxations", ctypes.c_int64), ("enqueues", ctypes.c_int64), ("ms", ctypes.c_double),
-                ("fixpoint_ms", ctypes.c_double)]
+                ("fixpoint_ms", ctypes.c_double), ("phases", ctypes.c_int32), ("trials", ctypes.c_int32),
+                ("phase_kind", ctypes.c_int32 * EG_MAX_PHASES), ("phase_cap", ctypes.c_int64 * EG_MAX_PHASES),
+                ("phase_rounds", ctypes.c_int64 * EG_MAX_PHASES),
+                ("phase_relaxations", ctypes.c_int64 * EG_MAX_PHASES),
+                ("phase_ms", ctypes.c_double * EG_MAX_PHASES)]
+
+    def phase_list(self) -> list[dict]:
+        """The recorded fixpoint launches: kind, cap, rounds, relaxations, ms."""
+        return [dict(kind=PHASE_NAMES.get(self.phase_kind[k], self.phase_kind[k]), cap=self.phase_cap[k],
+                     rounds=self.phase_rounds[k], relaxations=self.phase_relaxations[k], ms=self.phase_ms[k])
+                for k in range(self.phases)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("phase_")}
+        d["phase_list"] = self.phase_list()
+        return d
+
+
+class eg_server_counters(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "admitted", "solo", "taken_out", "completed", "refused",
+                                               "slices")]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EG_SRV_FAIL_RESERVATIONS = 1
 
 
 class EGError(RuntimeError):
@@ -74,6 +105,8 @@ SIGNATURES = {
     "eg_submit": (_I32, [_P, _P, _I32, _I64, _I64, ctypes.POINTER(ctypes.c_uint64)]),
     "eg_poll": (_I32, [_P, ctypes.c_uint64, _P, ctypes.POINTER(eg_stats)]),
     "eg_server_destroy": (_I32, [_P]),
+    "eg_server_counters_get": (_I32, [_P, ctypes.POINTER(eg_server_counters)]),
+    "eg_server_set_option": (_I32, [_P, _I32, _I64]),
     "eg_last_error": (ctypes.c_char_p, []),
     "eg_version": (ctypes.c_char_p, []),
 }
@@ -152,6 +185,8 @@ EG_OPT_SEED_MAX_PAIRS = 4
 EG_OPT_GRAPH = 5
 EG_OPT_CAP_CERTIFY = 6
 EG_OPT_CERTIFY_AFTER = 7
+EG_OPT_BLOCKS_PER_SM = 8
+EG_OPT_WAIT_LIMIT_US = 9
 
 
 def eg_solve_credit_noalloc(arena, credit_bits, w_scale, w_shift, credits_out, stream=None, max_rounds=0,
@@ -227,10 +262,11 @@ class Arena:
         return out, st
 
     def tune(self, local_windows=None, local_maxdeg=None, warm_start=None, seed_max_pairs=None, cap_certify=None,
-             certify_after=None):
+             certify_after=None, blocks_per_sm=None, wait_limit_us=None):
         for opt, val in ((EG_OPT_LOCAL_WINDOWS, local_windows), (EG_OPT_LOCAL_MAXDEG, local_maxdeg),
                          (EG_OPT_WARM_START, warm_start), (EG_OPT_SEED_MAX_PAIRS, seed_max_pairs),
-                         (EG_OPT_CAP_CERTIFY, cap_certify), (EG_OPT_CERTIFY_AFTER, certify_after)):
+                         (EG_OPT_CAP_CERTIFY, cap_certify), (EG_OPT_CERTIFY_AFTER, certify_after),
+                         (EG_OPT_BLOCKS_PER_SM, blocks_per_sm), (EG_OPT_WAIT_LIMIT_US, wait_limit_us)):
             if val is not None:
                 eg_set_option(self.handle, opt, int(val))
 
@@ -370,3 +406,13 @@ def eg_poll(server, ticket, credits_out=None):
 
 def eg_server_destroy(server) -> None:
     _check(load().eg_server_destroy(server))
+
+
+def eg_server_counters_get(server) -> dict:
+    c = eg_server_counters()
+    _check(load().eg_server_counters_get(server, ctypes.byref(c)))
+    return c.as_dict()
+
+
+def eg_server_set_option(server, option: int, value: int) -> None:
+    _check(load().eg_server_set_option(server, option, value))

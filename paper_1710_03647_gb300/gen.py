@@ -297,3 +297,23 @@ def config(idx: int, seed: int = 1, shrink: int = 1) -> Arena:
         side = 4000 // int(round(math.sqrt(shrink))) if shrink > 1 else 4000
         return grid_game(side, side, seed=seed, name=f"grid{side}_s{seed}")
     raise ValueError(idx)
+
+
+def _batch_game_job(args) -> Arena:
+    i, n, W, seed = args
+    return batch_game(i, n, W, seed)
+
+
+def batch_games(count: int = 4096, seed: int = 1, workers: int = 16) -> list[Arena]:
+    """The `count` games of the uneven batch (batch_shapes, batch_game).  Large
+    batches are drawn by a pool of spawned processes (spawned, so that no
+    CUDA state of the caller is forked); the result does not depend on it."""
+    import multiprocessing as mp
+    import os
+
+    jobs = [(i, n, W, seed) for i, (n, W) in enumerate(batch_shapes(count, seed=seed))]
+    workers = min(workers, os.cpu_count() or 1)
+    if len(jobs) <= 64 or workers <= 1:
+        return [_batch_game_job(j) for j in jobs]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_batch_game_job, jobs, chunksize=8)

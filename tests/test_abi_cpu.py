@@ -6,6 +6,7 @@ from __future__ import annotations
 import ctypes
 import os
 import re
+import subprocess
 
 import pytest
 
@@ -80,3 +81,18 @@ def test_missing_library_fails_loudly(tmp_path):
             eg.load(str(tmp_path / "nope.so"))
     finally:
         eg._lib = saved
+
+
+def test_stats_layout_matches_header(tmp_path):
+    # the binding's eg_stats must have the C struct's size and field offsets
+    src = tmp_path / "layout.c"
+    fields = [f for f, _ in eg.eg_stats._fields_]
+    body = "\n".join(f'printf("{f} %zu\\n", offsetof(eg_stats, {f}));' for f in fields)
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "eg.h"\nint main(void) {\n'
+                   f'printf("size %zu\\n", sizeof(eg_stats));\n{body}\nreturn 0;\n}}\n')
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    assert int(got["size"]) == ctypes.sizeof(eg.eg_stats)
+    for f in fields:
+        assert int(got[f]) == getattr(eg.eg_stats, f).offset, f

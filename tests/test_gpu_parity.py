@@ -361,21 +361,6 @@ def test_certified_caps_under_threshold_view(k):
         assert st.seeded <= int((f == TOP64).sum())
 
 
-def test_road_grid_full_size_fixpoint():
-    # 4000 x 4000 road-like grid (16M vertices, ~64.6M edges, int64 credits):
-    # too large for the oracle's Algorithm 1, so checked by properties that
-    # hold at any size: the credits satisfy every lift equation within
-    # {0..C} u {TOP}, and every TOP is a vertex the dual lift proved lost.
-    a = gen.config(3, 1)
-    out, st = gpu(a, 64)
-    assert st.status == eg.EG_OK and st.credit_bits == 64
-    code, bad = oracle.check(a.n, a.row_ptr, a.col, a.w, a.owner_bits, out, st.C)
-    assert code == 0, (code, bad)
-    ntop = int((out == TOP64).sum())
-    assert 0 < ntop < a.n
-    assert st.seeded == ntop
-
-
 def _ominus(a, b, C):
     if a == TOP64:
         return TOP64

@@ -48,17 +48,21 @@ def games():
 def test_mix_equals_alone():
     gs = games()
     arenas = [eg.Arena(g) for g in gs]
+    maps = lambda i: ((0, 1, 0), (32, 1, 0), (64, 256, (i - 2) * 100))  # noqa: E731
+    # each arena solved alone first: no arena is solved by the caller while
+    # a request for it is pending
+    want = {(i, m): alone(a.handle, *m, gs[i].n) for i, a in enumerate(arenas) for m in maps(i)}
     server = eg.eg_server_create(8 << 30, 16)
     try:
         reqs = []
         for i, (g, a) in enumerate(zip(gs, arenas)):
-            for bits, scale, shift in ((0, 1, 0), (32, 1, 0), (64, 256, (i - 2) * 100)):
-                reqs.append((i, bits, scale, shift, eg.eg_submit(server, a.handle, bits, scale, shift)))
-        for i, bits, scale, shift, t in reqs:
-            out = np.empty(gs[i].n, dtype=np.int32 if bits == 32 else np.int64)
+            for m in maps(i):
+                reqs.append((i, m, eg.eg_submit(server, a.handle, *m)))
+        for i, m, t in reqs:
+            out = np.empty(gs[i].n, dtype=np.int32 if m[0] == 32 else np.int64)
             rc, st = wait(server, t, out)
-            assert rc == eg.EG_OK, (i, bits, rc, eg.eg_last_error())
-            np.testing.assert_array_equal(out, alone(arenas[i].handle, bits, scale, shift, gs[i].n))
+            assert rc == eg.EG_OK, (i, m, rc, eg.eg_last_error())
+            np.testing.assert_array_equal(out, want[(i, m)])
             assert st.ms > 0
         # one more check against the oracle itself
         f, _ = oracle.solve(gs[2].n, gs[2].row_ptr, gs[2].col, gs[2].w, gs[2].owner_bits)
@@ -112,13 +116,14 @@ def test_arrivals_from_threads_while_batches_run():
 def test_budget_and_errors():
     small, big = gen.config(1, 3), gen.rmat_game(14, 8, seed=1)
     a_small, a_big = eg.Arena(small), eg.Arena(big)
+    want = alone(a_small.handle, 0, 1, 0, small.n)
     server = eg.eg_server_create(1 << 20, 8)  # 1 MiB: the small game fits, the big one does not
     try:
         t_big = eg.eg_submit(server, a_big.handle, 0, 1, 0)
         t_small = eg.eg_submit(server, a_small.handle, 0, 1, 0)
         out = np.empty(small.n, dtype=np.int64)
         assert wait(server, t_small, out)[0] == eg.EG_OK
-        np.testing.assert_array_equal(out, alone(a_small.handle, 0, 1, 0, small.n))
+        np.testing.assert_array_equal(out, want)
         assert wait(server, t_big)[0] == eg.EG_ERR_OOM
         rc, _ = eg.eg_poll(server, 987654321)
         assert rc == eg.EG_ERR_INVALID
@@ -150,22 +155,24 @@ def test_late_arrivals_join_the_running_solve():
     a_slow = eg.Arena(slow)
     a_slow.tune(cap_certify=0)  # keep it in the resident solve (no certified take-over)
     a_small = [eg.Arena(g) for g in smalls]
+    want_small = [alone(a.handle, 0, 1, 0, g.n) for g, a in zip(smalls, a_small)]
+    want_slow = alone(a_slow.handle, 64, 1, 0, slow.n)
     server = eg.eg_server_create(2 << 30, 8)
     try:
         t_slow = eg.eg_submit(server, a_slow.handle, 64, 1, 0)
         time.sleep(0.05)
         ts = [eg.eg_submit(server, a.handle, 0, 1, 0) for a in a_small]
-        for g, a, t in zip(smalls, a_small, ts):
+        for g, want, t in zip(smalls, want_small, ts):
             out = np.empty(g.n, dtype=np.int64)
             rc, st = wait(server, t, out)
             assert rc == eg.EG_OK, eg.eg_last_error()
-            np.testing.assert_array_equal(out, alone(a.handle, 0, 1, 0, g.n))
+            np.testing.assert_array_equal(out, want)
         rc, _ = eg.eg_poll(server, t_slow)
         assert rc == eg.EG_PENDING  # the small games did not wait for it
         out = np.empty(slow.n, dtype=np.int64)
         rc, st = wait(server, t_slow, out, timeout=120)
         assert rc == eg.EG_OK
-        np.testing.assert_array_equal(out, alone(a_slow.handle, 64, 1, 0, slow.n))
+        np.testing.assert_array_equal(out, want_slow)
         assert st.rounds > 0 and st.fixpoint_ms > 0
     finally:
         eg.eg_server_destroy(server)
@@ -209,17 +216,19 @@ def test_large_games_are_solved_alone_between_slices():
     smalls = [gen.config(1, 5), gen.rmat_game(12, 8, seed=6), gen.grid_game(24, 24, seed=3)]
     games = [big] + smalls
     arenas = [eg.Arena(g) for g in games]
+    maps = ((0, 1, 0), (32, 1, 0), (64, 4, 7))
+    want = {(i, m): alone(a.handle, *m, games[i].n) for i, a in enumerate(arenas) for m in maps}
     server = eg.eg_server_create(4 << 30, 8)
     try:
         reqs = []
         for i, a in enumerate(arenas):
-            for bits, scale, shift in ((0, 1, 0), (32, 1, 0), (64, 4, 7)):
-                reqs.append((i, bits, scale, shift, eg.eg_submit(server, a.handle, bits, scale, shift)))
-        for i, bits, scale, shift, t in reqs:
-            out = np.empty(games[i].n, dtype=np.int32 if bits == 32 else np.int64)
+            for m in maps:
+                reqs.append((i, m, eg.eg_submit(server, a.handle, *m)))
+        for i, m, t in reqs:
+            out = np.empty(games[i].n, dtype=np.int32 if m[0] == 32 else np.int64)
             rc, st = wait(server, t, out, timeout=120)
-            assert rc == eg.EG_OK, (i, bits, rc, eg.eg_last_error())
-            np.testing.assert_array_equal(out, alone(arenas[i].handle, bits, scale, shift, games[i].n))
+            assert rc == eg.EG_OK, (i, m, rc, eg.eg_last_error())
+            np.testing.assert_array_equal(out, want[(i, m)])
             assert st.ms > 0
     finally:
         eg.eg_server_destroy(server)

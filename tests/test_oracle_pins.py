@@ -248,3 +248,106 @@ def test_sweep_baseline_matches_algorithm_1(threads):
         a = _tiny(seed)
         g, _ = oracle.sweep(a.n, a.row_ptr, a.col, a.w, a.owner_bits, threads=threads)
         np.testing.assert_array_equal(g, oracle.brute_force(a.n, a.row_ptr, a.col, a.w, a.owner_bits))
+
+
+# ---- the certified composition of capped Algorithm 1 runs ------------------
+# oracle.certified_solve decides games by the two facts above; whatever trial
+# decides a game, the result must be the unique least EPM: the cap-C run of
+# Algorithm 1 on moderate games, brute force on tiny ones.
+
+def _certified(a, w=None):
+    return oracle.certified_solve(a.n, a.row_ptr, a.col, a.w if w is None else w, a.owner_bits)
+
+
+@pytest.mark.parametrize("make", [
+    lambda: gen.grid_game(32, 32, seed=1), lambda: gen.grid_game(48, 40, seed=2), lambda: gen.grid_game(64, 64, seed=3),
+    lambda: gen.config(1, 1), lambda: gen.config(1, 2), lambda: gen.rmat_game(10, 8, seed=3),
+    lambda: gen.varied_game(2000, 2, 16, 3000, seed=4), lambda: gen.varied_game(1500, 2, 6, 20, seed=5),
+], ids=["grid32", "grid48x40", "grid64", "uniform1k_s1", "uniform1k_s2", "rmat10", "varied2k_W3000", "varied1500_W20"])
+def test_certified_solve_matches_algorithm_1(make):
+    a = make()
+    f, st = _certified(a)
+    g, _ = solve(a)
+    np.testing.assert_array_equal(f, g)
+    assert st["trial"] >= -1
+
+
+def test_certified_solve_decides_grids_by_trials():
+    # the grids need the trials (B = 4 max|w| is far below C) and are decided by them
+    for seed in range(1, 5):
+        a = gen.grid_game(40, 40, seed=seed)
+        f, st = _certified(a)
+        assert st["trial"] >= 0 and st["B"] < st["C"]
+        np.testing.assert_array_equal(f, solve(a)[0])
+
+
+@pytest.mark.parametrize("k", [-128, -40, 0, 60, 127])
+def test_certified_solve_matches_algorithm_1_on_threshold_weights(k):
+    a = gen.rmat_game(10, 8, seed=6)
+    w2 = gen.threshold_weights(a.w, k, 100)
+    f, _ = _certified(a, w2)
+    g, _ = oracle.solve(a.n, a.row_ptr, a.col, w2, a.owner_bits)
+    np.testing.assert_array_equal(f, g)
+
+
+def test_certified_solve_matches_brute_force_on_tiny_games():
+    for seed in range(400):
+        a = _tiny(seed)
+        f, _ = oracle.certified_solve(a.n, a.row_ptr, a.col, a.w, a.owner_bits, cap_mult=1)
+        np.testing.assert_array_equal(f, oracle.brute_force(a.n, a.row_ptr, a.col, a.w, a.owner_bits))
+
+
+def test_certified_solve_zero_weight_cycle_is_a_player0_win():
+    # player 0 at vertex 0 can stay on the cycle 0 -> 1 -> 0 of weight 0
+    # (vertex 1 belongs to player 1 but has no other edge) or take the
+    # -1000 edge to the player-1 sink 2, which loops at weight -1.  The
+    # zero-weight cycle needs credit 0; it must not be mistaken for a loss
+    # (the dual's -1 per edge is what keeps it out of the dual's finite set).
+    a = arena_from_edges([0, 1, 1], [(0, 1, 5), (0, 2, -1000), (1, 0, -5), (2, 2, -1)])
+    f, st = oracle.certified_solve(a.n, a.row_ptr, a.col, a.w, a.owner_bits, cap_mult=1)
+    np.testing.assert_array_equal(f, [0, 5, TOP64])
+    np.testing.assert_array_equal(f, oracle.brute_force(a.n, a.row_ptr, a.col, a.w, a.owner_bits))
+
+
+# (3) In the dual game, vertices already proven lost may be replaced by sinks
+#     of value 0 (a self-loop of dual weight 0): a vertex finite in that
+#     modified dual is still won by player 1 in the game, since player 1
+#     either keeps the play on negative cycles or reaches a proven loss.
+
+def _dual_with_sinks(a, K, sinks):
+    w2, ob2 = _dual(a, K)
+    rp = np.asarray(a.row_ptr, dtype=np.int64)
+    rows_c, rows_w = [], []
+    for v in range(a.n):
+        if sinks[v]:
+            rows_c.append([v])
+            rows_w.append([0])
+        else:
+            rows_c.append(list(a.col[rp[v]:rp[v + 1]]))
+            rows_w.append(list(w2[rp[v]:rp[v + 1]]))
+    rp2 = np.zeros(a.n + 1, dtype=np.int64)
+    rp2[1:] = np.cumsum([len(r) for r in rows_c])
+    return (rp2, np.array([c for r in rows_c for c in r], dtype=np.int32),
+            np.array([x for r in rows_w for x in r], dtype=np.int64), ob2)
+
+
+@pytest.mark.parametrize("block", range(6))
+def test_dual_with_proven_losses_as_sinks_finds_only_losses(block):
+    checked = 0
+    for seed in range(block * 60, block * 60 + 60):
+        a = _tiny(seed)
+        exact = oracle.brute_force(a.n, a.row_ptr, a.col, a.w, a.owner_bits)
+        lost = exact == TOP64
+        if not lost.any():
+            continue
+        pick = gen.Stream(seed, 99).unit(a.n) < 0.5
+        maxw = max(1, int(np.abs(a.w).max()) if a.w.size else 1)
+        for sinks in (lost & pick, lost):
+            for K in (1, 8, a.n + 1):
+                rp2, col2, w2, ob2 = _dual_with_sinks(a, K, sinks)
+                for B in (maxw, 4 * maxw + 3):
+                    g, _ = oracle.solve(a.n, rp2, col2, w2, ob2, C=(K + 1) * B)
+                    fin = g != TOP64
+                    assert (exact[fin] == TOP64).all(), (seed, K, B)
+                    checked += 1
+    assert checked > 0

@@ -72,3 +72,57 @@ def test_noalloc_refuses_what_it_cannot_hold():
         with pytest.raises(eg.EGError) as ei:  # no widening buffer: 32 or 64 only
             eg.eg_solve_credit_noalloc(ar.handle, 0, 1, 0, dev)
         assert ei.value.status == eg.EG_ERR_INVALID
+
+
+def _certified_oracle(a):
+    import oracle
+
+    return oracle.certified_solve(a.n, a.row_ptr, a.col, a.w, a.owner_bits)[0]
+
+
+def test_noalloc_takes_the_certified_route_on_a_grid():
+    # a 512 x 512 road-like grid: the plain cap-C lifting would climb for
+    # hours; the allocation-free solve takes the same certified trials as
+    # eg_solve_credit and reaches the same credits
+    a = gen.grid_game(512, 512, seed=2)
+    with eg.Arena(a) as ar:
+        want = torch.empty(a.n, dtype=torch.int64, device="cuda:0")
+        _, st_a = eg.eg_solve_credit(ar.handle, 64, 1, 0, want)
+        for call in range(2):
+            got = torch.full((a.n,), -7, dtype=torch.int64, device="cuda:0")
+            rc, st = eg.eg_solve_credit_noalloc(ar.handle, 64, 1, 0, got, max_rounds=200000)
+            assert rc == eg.EG_OK and st.status == eg.EG_OK
+            assert st.trials >= 1 and st.phases >= 3
+            np.testing.assert_array_equal(got.cpu().numpy(), want.cpu().numpy(), err_msg=f"call {call}")
+        np.testing.assert_array_equal(want.cpu().numpy(), _certified_oracle(a))
+
+
+def test_noalloc_budget_leaves_credits_below_the_fixpoint():
+    a = gen.grid_game(256, 256, seed=1)
+    with eg.Arena(a) as ar:
+        want = torch.empty(a.n, dtype=torch.int64, device="cuda:0")
+        eg.eg_solve_credit(ar.handle, 64, 1, 0, want)
+        ref = want.cpu().numpy()
+        for rounds in (1, 12):
+            got = torch.full((a.n,), -7, dtype=torch.int64, device="cuda:0")
+            rc, st = eg.eg_solve_credit_noalloc(ar.handle, 64, 1, 0, got, max_rounds=rounds, raise_on_error=False)
+            assert st.status == rc
+            g = got.cpu().numpy()
+            if rounds == 1 or rc != eg.EG_OK:  # one round cannot reach the fixpoint of this grid
+                assert rc == eg.EG_ERR_BUDGET
+                assert (g >= 0).all() and (g <= ref).all()
+            else:
+                np.testing.assert_array_equal(g, ref)
+        got = torch.empty(a.n, dtype=torch.int64, device="cuda:0")
+        rc, st = eg.eg_solve_credit_noalloc(ar.handle, 64, 1, 0, got)
+        assert rc == eg.EG_OK
+        np.testing.assert_array_equal(got.cpu().numpy(), ref)
+
+
+def test_noalloc_refuses_misaligned_output():
+    small = gen.config(1, 3)
+    with eg.Arena(small) as ar:
+        buf = torch.empty(small.n + 1, dtype=torch.int64, device="cuda:0")
+        with pytest.raises(eg.EGError) as ei:  # 4 bytes off an 8-byte boundary
+            eg.eg_solve_credit_noalloc(ar.handle, 64, 1, 0, buf.data_ptr() + 4)
+        assert ei.value.status == eg.EG_ERR_INVALID and "aligned" in str(ei.value)
