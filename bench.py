@@ -1,18 +1,23 @@
 #!/usr/bin/env python3
-"""Benchmark: least-fixpoint lifting of the energy progress measure on one
-R-MAT energy game (2^20 vertices, ~8.8M edges, weights in [-100, 100],
-int32 credits), solved to the fixpoint per step.
+"""Benchmark: least-fixpoint lifting of the energy progress measure on the
+4000 x 4000 road-like grid game (16M vertices, 64.6M edges, weights in
+[-1000, 1000] with 40% negative, int64 credits), solved to the exact fixpoint
+per step by eg_solve_credit's default route (a short cap-C attempt, then
+certified trial caps).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  Metric: edge-relaxations/s, i.e. evaluations
 of f(u) (-) w over edges (pulls of player-0 lifts plus pushes to
 predecessors) divided by the device time of the solve; time-to-fixpoint per
-step is ms_per_step.  The arena is resident in HBM before the timed region;
-between timed steps a 512 MiB buffer is rewritten to flush L2.
+step is ms_per_step, shown beside the CPU oracle's time on the same game.
+The arena is resident in HBM before the timed region; between timed steps a
+512 MiB buffer is rewritten to flush L2 (the arena and state, ~3.5 GB, are
+larger than L2 anyway).
 
---impl reference times the CPU oracle (Algorithm 1, single thread) on a
-bounded sample: the same generator at 2^16 vertices per step.
+--impl reference times the CPU oracle on a bounded sample of the same
+workload: the same generator at 700 x 700 per step, solved exactly by the
+oracle's certified composition of Algorithm 1 runs.
 
 A single game does not shard: with --gpus N every rank solves its own
 replica (no collective on the data path) and value sums the ranks' work
@@ -34,16 +39,32 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(workload="rmat20_s1: R-MAT scale 20 (a,b,c,d)=(.57,.19,.19,.05), 8*2^20 draws, "
-                         "w uniform in [-100,100], owner Bernoulli(0.5), seed 1",
-                scale=20, seed=1, credit_bits=32)
+WORKLOAD = dict(workload="grid4000_s1: 4000x4000 grid, 4-neighbour directed edges + 1% uniform long edges, "
+                         "w negative w.p. 0.4 (uniform in [-1000,-1]) else uniform in [0,1000], "
+                         "owner Bernoulli(0.5), seed 1",
+                side=4000, seed=1, credit_bits=64, golden="grid4000_s1")
+CONTEXT_RMAT = dict(workload="rmat20_s1: R-MAT scale 20 (a,b,c,d)=(.57,.19,.19,.05), 8*2^20 draws, "
+                             "w uniform in [-100,100], owner Bernoulli(0.5), seed 1",
+                    scale=20, seed=1, credit_bits=32, golden="rmat20_s1")
+SAMPLE_SIDE = 700      # the reference arm's per-step sample of the headline workload
+BASELINE_SIDE = 1000   # cpu_baseline's sample (one solve, ~6-10 s)
 METRIC = "edge-relaxations/s"
 UNIT = "relax/s"
+
+
 # algorithmic bytes (per unit): relaxation = index 4 + weight 4 + credit s;
 # list entry (lift or push) = two offsets 8 + entry 4 + credit s;
 # enqueue = entry write 4 + bitmap word 4
 def algorithmic_bytes(st, s):
     return st["relaxations"] * (8 + s) + (st["lifts"] + st["pushes"]) * (12 + s) + st["enqueues"] * 8
+
+
+def launches_of(st):
+    """Kernels of one single-game solve: warm start, init and the fixpoint per
+    fixpoint launch, plus the trials' bitmap passes (3 after a capped lift,
+    2 after a dual lift)."""
+    kinds = [p["kind"] for p in st["phase_list"]]
+    return 3 * len(kinds) + 3 * kinds.count("capped") + 2 * kinds.count("dual")
 
 
 def strip_comments(src):
@@ -170,50 +191,54 @@ def dist_setup():
     return world, rank, local
 
 
+def oracle_work(st):
+    """Edge evaluations of the oracle: lift edges, predecessor scans, recounts."""
+    return st["lift_edge_evals"] + st["pre_scans"] + st["recount_evals"]
+
+
 def run_reference(args, world, rank):
+    """The CPU oracle (certified composition of Algorithm 1 runs, one
+    thread) on a bounded sample of the headline workload per step."""
     if rank != 0:
         return
     import oracle
     from paper_1710_03647_gb300 import gen
 
-    sample_scale = 16
-    a = gen.rmat_game(sample_scale, 8, seed=WORKLOAD["seed"])
-    C = oracle.bound(a.n, a.row_ptr, a.w)
+    a = gen.grid_game(SAMPLE_SIDE, SAMPLE_SIDE, seed=WORKLOAD["seed"])
     times, relax = [], []
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        _, st = oracle.solve(a.n, a.row_ptr, a.col, a.w, a.owner_bits, C)
+        _, st = oracle.certified_solve(a.n, a.row_ptr, a.col, a.w, a.owner_bits)
         dt = time.perf_counter() - t0
         if k >= args.warmup:
             times.append(dt)
-            relax.append(st["lift_edge_evals"] + st["pre_scans"] + st["recount_evals"])
+            relax.append(oracle_work(st))
     value = sum(relax) / sum(times)
-    sample = (f"oracle (Algorithm 1, 1 thread) on R-MAT scale {sample_scale} (n={a.n}, m={a.m}), "
-              f"same generator and seed, one full solve per step")
+    sample = (f"oracle (certified composition of Algorithm 1 runs, 1 thread) on the {SAMPLE_SIDE}x{SAMPLE_SIDE} grid "
+              f"(n={a.n}, m={a.m}) from the same generator and seed, one exact solve per step")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-        "data": "synthetic", "config": {"workload": WORKLOAD["workload"], "sample_scale": sample_scale},
+        "data": "synthetic", "config": {"workload": WORKLOAD["workload"], "sample": f"{SAMPLE_SIDE}x{SAMPLE_SIDE}"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
 
 def cpu_baseline():
-    """The oracle as it stands, single-threaded, on a bounded sample (~10-30 s)."""
+    """The oracle as it stands, single-threaded, on a bounded sample (~10 s)."""
     import oracle
     from paper_1710_03647_gb300 import gen
 
-    scale = 16
-    a = gen.rmat_game(scale, 8, seed=WORKLOAD["seed"])
+    a = gen.grid_game(BASELINE_SIDE, BASELINE_SIDE, seed=WORKLOAD["seed"])
     t0 = time.perf_counter()
-    _, st = oracle.solve(a.n, a.row_ptr, a.col, a.w, a.owner_bits)
+    _, st = oracle.certified_solve(a.n, a.row_ptr, a.col, a.w, a.owner_bits)
     dt = time.perf_counter() - t0
-    relax = st["lift_edge_evals"] + st["pre_scans"] + st["recount_evals"]
-    return {"value": relax / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"R-MAT scale {scale} (n={a.n}, m={a.m}) from the same generator, one full solve "
-                      f"({dt:.1f} s, {relax} edge evaluations)"}
+    return {"value": oracle_work(st) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{BASELINE_SIDE}x{BASELINE_SIDE} grid (n={a.n}, m={a.m}) from the headline's generator, one "
+                      f"exact solve by the oracle's certified composition of Algorithm 1 runs ({dt:.1f} s, "
+                      f"{oracle_work(st)} edge evaluations)"}
 
 
 def ev_pair():
@@ -222,34 +247,78 @@ def ev_pair():
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def large_single_game(eg, gen, torch, dev, stream, flush):
-    """4000 x 4000 road-like grid (16M vertices, ~64.6M edges, int64 credits)
-    solved once to the exact fixpoint with the default options."""
-    a = gen.config(3, 1)
+def golden(name):
+    path = os.path.join(ROOT, "tests", "golden", f"{name}.json")
+    return json.load(open(path)) if os.path.exists(path) else None
+
+
+def traffic_record(name):
+    """DRAM bytes per fixpoint launch from the committed ncu record, or None
+    when the kernel sources changed since it was taken."""
+    prof = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(prof):
+        return None
+    rec = json.load(open(prof))
+    if rec.get("kernel_source_sha256") != kernel_source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def rmat_context(eg, gen, torch, dev, stream, flush, plain_start=True, tune=True):
+    """Config 2 (R-MAT scale 20, int32): time to the fixpoint, relaxations/s
+    and the fixpoint kernel against HBM, beside the oracle's stored time on
+    the same game; optionally the paper's f = 0 start."""
+    a = gen.rmat_game(CONTEXT_RMAT["scale"], 8, seed=CONTEXT_RMAT["seed"])
+    bits = CONTEXT_RMAT["credit_bits"]
+    s = bits // 8
     arena = eg.Arena(a)
-    out = torch.empty(a.n, dtype=torch.int64, device=dev)
+    out = torch.empty(a.n, dtype=torch.int32, device=dev)
+    for _ in range(3):
+        eg.eg_solve_credit(arena.handle, bits, 1, 0, out, stream=stream.cuda_stream)
+    tuning = None
+    if tune:
+        import tempfile
+
+        with tempfile.TemporaryDirectory() as td:
+            tuning = eg.eg_autotune(arena.handle, bits, 1, 0, os.path.join(td, "plans.jsonl"), max_solves=60)
     res = []
-    for k in range(2):
+    for k in range(10):
         with torch.cuda.stream(stream):
             flush.fill_(k)
         b, e = ev_pair()
         b.record(stream)
-        _, st = eg.eg_solve_credit(arena.handle, 64, 1, 0, out, stream=stream.cuda_stream)
+        _, st = eg.eg_solve_credit(arena.handle, bits, 1, 0, out, stream=stream.cuda_stream)
         e.record(stream)
         torch.cuda.synchronize()
         res.append((b.elapsed_time(e), st.as_dict()))
-    arena.close()
-    ms, st = min(res, key=lambda x: x[0])
-    return {"workload": "grid4000_s1: 4000x4000 grid, 4-neighbour edges + 1% long edges, w in [-1000,1000] "
-                        "with 40% negative, owner Bernoulli(0.5), seed 1",
-            "n": a.n, "m": a.m, "credit_bits": 64, "time_to_fixpoint_ms": ms, "rounds": st["rounds"],
-            "relaxations": st["relaxations"], "lifts": st["lifts"], "proven_player1": st["seeded"],
-            "relax_per_s": st["relaxations"] / (st["fixpoint_ms"] * 1e-3),
-            "roofline_frac": algorithmic_bytes(st, 8) / (st["fixpoint_ms"] * 1e-3) / 1e9 / peaks()[0],
-            "C": st["C"], "note": "certified trial caps (default); best of 2 solves"}
+    ms = statistics.median(r[0] for r in res)
+    relax = sum(r[1]["relaxations"] for r in res)
+    fix_ms = sum(r[1]["fixpoint_ms"] for r in res)
+    bytes_alg = sum(algorithmic_bytes(r[1], s) for r in res)
+    peak, peak_kind = peaks()
+    g = golden(CONTEXT_RMAT["golden"])
+    out_d = {"workload": CONTEXT_RMAT["workload"], "n": a.n, "m": a.m, "credit_bits": bits,
+             "time_to_fixpoint_ms": ms, "relax_per_s": relax / (sum(r[0] for r in res) * 1e-3),
+             "rounds": res[-1][1]["rounds"], "relaxations_per_solve": res[-1][1]["relaxations"],
+             "roofline": {"bound": "hbm", "achieved": bytes_alg / (fix_ms * 1e-3) / 1e9, "peak": peak,
+                          "unit": "GB/s", "frac": bytes_alg / (fix_ms * 1e-3) / 1e9 / peak, "peak_kind": peak_kind,
+                          "traffic": traffic_record("fixpoint_rmat20_traffic.json"), "kernel": "k_fixpoint"},
+             "oracle": None, "settings": "autotuned (eg_autotune)" if tuning else "defaults", "tuning": tuning}
+    if g:
+        out_d["oracle"] = {"time_to_fixpoint_s": g["oracle_seconds"], "route": "Algorithm 1 with cap C, 1 thread",
+                           "edge_evaluations": g["oracle_lift_edge_evals"] + g["oracle_pre_scans"],
+                           "speedup": g["oracle_seconds"] * 1e3 / ms}
+    if plain_start:
+        arena.tune(warm_start=0)
+        _, pst = eg.eg_solve_credit(arena.handle, bits, 1, 0, out, stream=stream.cuda_stream)
+        arena.tune(warm_start=1)
+        pd = pst.as_dict()
+        out_d["plain"] = {"time_to_fixpoint_ms": pd["ms"], "relaxations": pd["relaxations"], "rounds": pd["rounds"],
+                          "note": "same solver, warm start and certified trials off (f = 0 start as in the paper)"}
+    return arena, a, out_d
 
 
-def batch_games(eg, gen, torch, dev, stream, count):
+def batch_games(eg, gen, torch, dev, stream, count, tune=True):
     """`count` uneven games (n log-uniform in [1k, 200k], out-degree uniform
     in [2, 16], weights in [-W, W], W log-uniform in [10, 10^4]): all in one
     persistent launch (a plan over one packed arena) vs one solve per game."""
@@ -260,6 +329,12 @@ def batch_games(eg, gen, torch, dev, stream, count):
     plan = eg.Plan(h, count)
     bout = torch.empty(plan.total, dtype=torch.int64, device=dev)
     plan.run(bout, stream=stream.cuda_stream)
+    tuning = None
+    if tune:
+        import tempfile
+
+        with tempfile.TemporaryDirectory() as td:
+            tuning = eg.eg_plan_autotune(plan, os.path.join(td, "plans.jsonl"), max_solves=30)
     bms = []
     for _ in range(3):
         b, e = ev_pair()
@@ -299,7 +374,7 @@ def batch_games(eg, gen, torch, dev, stream, count):
             "batched_ms": bmed, "batched_games_per_s": count / (bmed * 1e-3), "batched_relaxations": bst.relaxations,
             "per_game_total_ms": total, "per_game_games_per_s": count / (total * 1e-3),
             "per_game_p50_ms": lat[len(lat) // 2], "per_game_p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-            "batched_equals_per_game": bool(same),
+            "batched_equals_per_game": bool(same), "plan_tuning": tuning,
             "note": "batched: one plan (one persistent launch, CUDA graph replay) over a packed arena; latency of "
                     "every game in the batch = the batch time"}
 
@@ -401,20 +476,21 @@ def serving(eg, gen, torch, dev, stream, per_rate, scales=(10, 21), seed=11):
 
 def cpu_parallel_baseline():
     """The paper's Algorithm 2 (OpenMP lifting sweeps from f = 0) on all host
-    cores, on the same bounded sample as cpu_baseline: context for the
-    paper's multi-core CPU column."""
+    cores, on R-MAT scale 16 from the config-2 context's generator: context
+    for the paper's multi-core CPU column (on the grid the sweeps from f = 0
+    climb pseudo-polynomially and do not finish)."""
     import oracle
     from paper_1710_03647_gb300 import gen
 
     scale = 16
-    a = gen.rmat_game(scale, 8, seed=WORKLOAD["seed"])
+    a = gen.rmat_game(scale, 8, seed=CONTEXT_RMAT["seed"])
     t0 = time.perf_counter()
     _, st = oracle.sweep(a.n, a.row_ptr, a.col, a.w, a.owner_bits, threads=os.cpu_count() or 1)
     dt = time.perf_counter() - t0
     return {"value": st["edge_evals"] / dt, "unit": UNIT, "cores": st["threads"],
             "kind": "paper Algorithm 2 (parallel lifting sweeps)", "time_to_fixpoint_s": dt,
             "sweeps": st["sweeps"],
-            "sample": f"R-MAT scale {scale} (n={a.n}, m={a.m}) from the same generator, f = 0 start, one full solve"}
+            "sample": f"R-MAT scale {scale} (n={a.n}, m={a.m}), f = 0 start, one full solve"}
 
 
 def main():
@@ -423,10 +499,13 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--side", type=int, default=WORKLOAD["side"], help="grid side of the headline (4000 = config 3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-context", action="store_true", help="skip the R-MAT scale-20 context (config 2)")
     ap.add_argument("--no-plain", action="store_true", help="skip the context solve without warm start")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched threshold-query comparison")
-    ap.add_argument("--no-large", action="store_true", help="skip the 4000x4000 grid solve")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
+    ap.add_argument("--no-tune", action="store_true", help="time the default settings (no eg_autotune)")
     ap.add_argument("--batch-games", type=int, default=4096, help="games in the batched-vs-per-game comparison "
                     "(4096 = the full workload; 0 skips it)")
     ap.add_argument("--serve-requests", type=int, default=512, help="requests per arrival rate (0 skips serving)")
@@ -450,7 +529,8 @@ def main():
     __graft_entry__.build()
     from paper_1710_03647_gb300 import eg, gen
 
-    a = gen.rmat_game(WORKLOAD["scale"], 8, seed=WORKLOAD["seed"])
+    side = args.side
+    a = gen.grid_game(side, side, seed=WORKLOAD["seed"])
     bits = WORKLOAD["credit_bits"]
     if rank == 0:
         print(f"[bench] workload ready n={a.n} m={a.m}", file=sys.stderr, flush=True)
@@ -458,12 +538,23 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    out = torch.empty(a.n, dtype=torch.int32 if bits == 32 else torch.int64, device=dev)
+    out = torch.empty(a.n, dtype=torch.int64, device=dev)
     arena = eg.Arena(a)
 
     def step():
         _, st = eg.eg_solve_credit(arena.handle, bits, 1, 0, out, stream=stream.cuda_stream)
         return st
+
+    # launch settings picked by the library's autotuner (timed solves, each
+    # exact), outside the timed region; a fresh cache file, so it searches
+    tuning = None
+    if not args.no_tune:
+        import tempfile
+
+        t0 = time.perf_counter()
+        with tempfile.TemporaryDirectory() as td:
+            tuning = eg.eg_autotune(arena.handle, bits, 1, 0, os.path.join(td, "plans.jsonl"), max_solves=40)
+        tuning["search_s"] = time.perf_counter() - t0
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     stats = []
@@ -489,58 +580,65 @@ def main():
     step_ms = [b.elapsed_time(e) for b, e in ev]
     total_ms = sum(step_ms)
     relax = sum(x["relaxations"] for x in stats)
-    launches = 3 * args.steps  # warm-start seed + init + persistent fixpoint per step
+    launches = sum(launches_of(x) for x in stats)
     if pg:
         total_ms_max, relax_all = reduce_over_ranks(total_ms, relax, dev, pg)
     else:
         total_ms_max, relax_all = total_ms, float(relax)
+    ok = all(x["status"] == 0 for x in stats)
 
-    # dominant kernel: the persistent fixpoint; its duration from CUDA events
-    # recorded around its launch on this stream
+    # dominant kernel: the persistent fixpoint; the library times every launch
+    # of it with CUDA events on the solve's stream (phase_ms), summed here over
+    # all launches of all timed steps
     fix_ms = sum(x["fixpoint_ms"] for x in stats)
+    n_launch = sum(x["phases"] for x in stats)
     bytes_alg = sum(algorithmic_bytes(x, s) for x in stats)
     peak, peak_kind = peaks()
     achieved = bytes_alg / (fix_ms * 1e-3) / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "fixpoint_rmat20_traffic.json")
-    if os.path.exists(prof):
-        rec = json.load(open(prof))
-        # counters taken on another version of the kernel say nothing about this one
-        if rec.get("kernel_source_sha256") == kernel_source_hash():
-            traffic = rec.get("dram_bytes_per_launch")
+    traffic = traffic_record(f"fixpoint_grid{side}_traffic.json")
 
     # end to end through the public API: the arena from pinned host arrays
     # (eg_create copies them and builds the reverse CSR on the device), one
     # solve, the credits back to a pinned host array
     e2e = None
-    if rank == 0:
+    if rank == 0 and not args.no_e2e:
         def pinned(x):
             return torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
 
         rp_h = pinned(np.asarray(a.row_ptr, dtype=np.int64))
         col_h, w_h = pinned(np.asarray(a.col, dtype=np.int32)), pinned(np.asarray(a.w, dtype=np.int32))
         ob_h = pinned(np.asarray(a.owner_bits, dtype=np.uint32).view(np.int32))
-        host_out = torch.empty(a.n, dtype=torch.int32 if bits == 32 else torch.int64).pin_memory()
-        e_times, e_relax = [], 0
-        for k in range(max(3, args.steps // 2)):
+        host_out = torch.empty(a.n, dtype=torch.int64).pin_memory()
+        e_times, e_relax, e_create = [], 0, []
+        for k in range(5):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             h = eg.eg_create(a.n, a.m, rp_h, col_h, w_h, owner_bits=ob_h)
+            t1 = time.perf_counter()
             _, st = eg.eg_solve_credit(h, bits, 1, 0, host_out)
             eg.eg_destroy(h)
             e_times.append(time.perf_counter() - t0)
+            e_create.append(t1 - t0)
             e_relax += st.relaxations
         h2d = sum(t.numel() * t.element_size() for t in (rp_h, col_h, w_h, ob_h))
         e2e = {"value": e_relax / sum(e_times), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(host_out.numel() * host_out.element_size() + 128),
-               "ms_per_step": 1e3 * sum(e_times) / len(e_times), "host_buffers": "pinned"}
+               "ms_per_step": 1e3 * sum(e_times) / len(e_times),
+               "eg_create_ms": 1e3 * statistics.median(e_create), "host_buffers": "pinned"}
 
-    # 256 mean-payoff threshold queries on the same arena (w' = 256 w - k W,
+    single = world == 1
+    context = None
+    rarena = None
+    if single and not args.no_context:
+        rarena, ra, context = rmat_context(eg, gen, torch, dev, stream, flush, plain_start=not args.no_plain,
+                                           tune=not args.no_tune)
+
+    # 256 mean-payoff threshold queries on the R-MAT arena (w' = 256 w - k W,
     # k = -128..127, W = 100): one batched launch vs one solve per query
     thresholds = None
-    if world == 1 and not args.no_batch:
+    if rarena is not None and not args.no_batch:
         ks = list(range(-128, 128))
-        plan = eg.Plan(arena.handle, len(ks), part=[0] * len(ks), w_scale=[256] * len(ks),
+        plan = eg.Plan(rarena.handle, len(ks), part=[0] * len(ks), w_scale=[256] * len(ks),
                        w_shift=[k * 100 for k in ks])
         bout = torch.empty(plan.total, dtype=torch.int64, device=dev)
         for _ in range(2):
@@ -549,19 +647,19 @@ def main():
         for _ in range(3):
             with torch.cuda.stream(stream):
                 flush.fill_(1)
-            b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            b0, b1 = ev_pair()
             b0.record(stream)
             _, bst = plan.run(bout, stream=stream.cuda_stream)
             b1.record(stream)
             torch.cuda.synchronize()
             bms.append(b0.elapsed_time(b1))
             brelax = bst.relaxations
-        one = torch.empty(a.n, dtype=torch.int64, device=dev)
+        one = torch.empty(ra.n, dtype=torch.int64, device=dev)
         qms = []
         for k in ks:
-            q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            q0, q1 = ev_pair()
             q0.record(stream)
-            eg.eg_solve_credit(arena.handle, 64, 256, k * 100, one, stream=stream.cuda_stream)
+            eg.eg_solve_credit(rarena.handle, 64, 256, k * 100, one, stream=stream.cuda_stream)
             q1.record(stream)
             torch.cuda.synchronize()
             qms.append(q0.elapsed_time(q1))
@@ -575,26 +673,12 @@ def main():
                       "per_query_p99_ms": qms_sorted[min(len(qms) - 1, int(0.99 * len(qms)))],
                       "note": "batched: all queries in one persistent launch (CUDA graph); latency of every "
                               "query = the batch time"}
+    if rarena is not None:
+        rarena.close()
 
-    # the paper's start (f = 0 everywhere, no warm start), once, for context
-    plain = None
-    if world == 1 and not args.no_plain:
-        arena.tune(warm_start=0)
-        _, pst = eg.eg_solve_credit(arena.handle, bits, 1, 0, out, stream=stream.cuda_stream)
-        arena.tune(warm_start=1)
-        pd = pst.as_dict()
-        plain = {"time_to_fixpoint_ms": pd["ms"], "relaxations": pd["relaxations"], "rounds": pd["rounds"],
-                 "relax_per_s": pd["relaxations"] / (pd["fixpoint_ms"] * 1e-3),
-                 "roofline_frac": algorithmic_bytes(pd, s) / (pd["fixpoint_ms"] * 1e-3) / 1e9 / peaks()[0],
-                 "note": "same solver, warm start off (f = 0 start as in the paper)"}
-
-    large = batch = served = None
-    # the context sections run once, in single-GPU runs (replica runs time the headline only)
-    single = world == 1
-    if single and not args.no_large:
-        large = large_single_game(eg, gen, torch, dev, stream, flush)
+    batch = served = None
     if single and args.batch_games > 0:
-        batch = batch_games(eg, gen, torch, dev, stream, args.batch_games)
+        batch = batch_games(eg, gen, torch, dev, stream, args.batch_games, tune=not args.no_tune)
     if single and args.serve_requests > 0:
         served = serving(eg, gen, torch, dev, stream, args.serve_requests)
 
@@ -603,34 +687,42 @@ def main():
         if pg:
             pg.destroy_process_group()
         return
-    golden = os.path.join(ROOT, "tests", "golden", "rmat20_s1.json")
-    oracle_relax = None
-    if os.path.exists(golden):
-        g = json.load(open(golden))
-        oracle_relax = g["oracle_lift_edge_evals"] + g["oracle_pre_scans"]
+    g = golden(WORKLOAD["golden"]) if side == WORKLOAD["side"] else None
+    oracle_ref = None
+    if g:
+        oracle_ref = {"time_to_fixpoint_s": g["oracle_seconds"], "edge_evaluations": g["oracle_lift_edge_evals"] +
+                      g["oracle_pre_scans"], "route": "certified composition of Algorithm 1 runs, 1 thread "
+                      "(Algorithm 1 with cap C alone would need ~1e14 lifts)", "trial": g["trial"],
+                      "speedup": g["oracle_seconds"] * 1e3 / statistics.median(step_ms)}
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline()
     cpu_par = None if args.no_cpu_baseline or world > 1 else cpu_parallel_baseline()
     st0 = stats[-1]
     line = {
         "metric": METRIC, "value": relax_all / (total_ms_max * 1e-3), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32" if bits == 32 else "int64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD["workload"], "n": a.n, "m": a.m, "credit_bits": bits,
-                   "parallelism": "replicas" if world > 1 else "single", "l2": "flushed between steps (512 MiB write)"},
+        "config": {"workload": WORKLOAD["workload"] if side == WORKLOAD["side"] else f"grid{side}_s1",
+                   "n": a.n, "m": a.m, "credit_bits": bits,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed between steps (512 MiB write); arena and state exceed L2"},
+        "all_exact": ok,
+        "settings": "autotuned (eg_autotune)" if tuning else "defaults",
+        "tuning": tuning,
         "time_to_fixpoint_ms": statistics.median(step_ms),
+        "oracle": oracle_ref,
         "rounds": st0["rounds"], "relaxations_per_step": st0["relaxations"], "lifts": st0["lifts"],
-        "pushes": st0["pushes"], "oracle_relaxations": oracle_relax,
+        "pushes": st0["pushes"], "trials": st0["trials"], "phases": st0["phase_list"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "kernel": "k_fixpoint", "peak_kind": peak_kind,
-                     "algorithmic_bytes_per_launch": bytes_alg / args.steps,
-                     "kernel_ms_per_launch": fix_ms / args.steps},
+                     "launches_per_step": n_launch / args.steps,
+                     "algorithmic_bytes_per_launch": bytes_alg / n_launch,
+                     "kernel_ms_per_launch": fix_ms / n_launch},
         "cpu_baseline": cpu,
         "cpu_parallel_baseline": cpu_par,
-        "warm_start_seeded": st0["seeded"],
-        "plain": plain,
+        "proven_player1": st0["seeded"],
+        "rmat_context": context,
         "threshold_queries": thresholds,
-        "large_single_game": large,
         "batch_games": batch,
         "serving": served,
         "e2e": e2e,

@@ -309,6 +309,43 @@ eg_status eg_solve_credit_noalloc(eg_arena *arena, int32_t credit_bits, int64_t 
                                   void *credits_out, eg_stats *st, void *cuda_stream, int64_t max_rounds);
 
 /*
+ * Autotuning of the launch settings (no counterpart in the paper, whose
+ * closing remarks propose customising the launch configuration from an
+ * analysis of the input).  The settings of eg_set_option that change only
+ * how fast the least fixpoint is reached -- EG_OPT_LOCAL_WINDOWS,
+ * EG_OPT_LOCAL_MAXDEG, EG_OPT_BLOCKS_PER_SM and, when the certified trials
+ * run, EG_OPT_CAP_CERTIFY and EG_OPT_CERTIFY_AFTER -- are chosen by timing
+ * real solves (every one of them exact) in a coordinate search that starts
+ * from the arena's current settings; a candidate replaces the best so far
+ * only if it is more than 3% faster.  The chosen settings are set on the
+ * arena (for eg_plan_autotune, on the plan's arena) and returned.
+ *
+ * cache_path (may be NULL): a text file of JSON lines, one per signature.
+ * The signature (key) of an instance is its log2 vertex count, mean degree,
+ * coarse log2 histograms of out- and in-degrees, credit width and
+ * log2(C / max|w'|), prefixed by "plan<count>-" for plans.  A signature
+ * found in the file takes its settings without timing anything
+ * (from_cache = 1); otherwise the search runs and its result is written to
+ * the file (replacing the file atomically).
+ *
+ * max_solves: bound on timed runs (0: 60).  Allocates a device buffer for
+ * the timed runs' credits and a private stream; synchronous.  Solves and
+ * plan runs of the arena must not run concurrently with it.
+ */
+typedef struct eg_tuning {
+    int32_t local_windows, local_maxdeg, blocks_per_sm, cap_certify;
+    int64_t certify_after;
+    double default_ms;   /* time to the fixpoint with the settings the search started from (-1: cached) */
+    double tuned_ms;     /* with the chosen settings (the cached figure when from_cache) */
+    int32_t solves;      /* runs timed by this call */
+    int32_t from_cache;  /* 1: the settings came from cache_path */
+    char key[96];        /* the signature */
+} eg_tuning;
+eg_status eg_autotune(eg_arena *arena, int32_t credit_bits, int64_t w_scale, int64_t w_shift, const char *cache_path,
+                      int32_t max_solves, eg_tuning *out);
+eg_status eg_plan_autotune(eg_plan *plan, const char *cache_path, int32_t max_solves, eg_tuning *out);
+
+/*
  * Serving, with continuous batching.  A server owns a scheduler thread, a
  * pool of device memory of about device_mem_budget bytes (taken at
  * eg_server_create: about 35% for vertex slots at 74 bytes each, 65% for

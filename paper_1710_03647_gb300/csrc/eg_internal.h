@@ -166,4 +166,8 @@ eg_status plan_create(eg_arena *ar, int count, const int32_t *part, const int64_
 eg_status plan_run(eg_plan_impl *p, void *out, eg_stats *st, cudaStream_t user, long long max_rounds);
 eg_status plan_release(eg_plan_impl *p);
 void plan_instance_info(const eg_plan_impl *p, int i, long long *offset, long long *n, long long *C, int *bits);
+eg_plan_impl *plan_impl(eg_plan *plan);
+eg_arena *plan_arena(const eg_plan_impl *p);
+int plan_count(const eg_plan_impl *p);
+int plan_bits(const eg_plan_impl *p);  // the width the plan computes in
 }  // namespace eg

@@ -2098,6 +2098,13 @@ eg_status plan_run(eg_plan_impl *p, void *out, eg_stats *st, cudaStream_t user, 
 
 struct eg_plan : eg::eg_plan_impl {};
 
+namespace eg {
+eg_plan_impl *plan_impl(eg_plan *plan) { return plan; }
+eg_arena *plan_arena(const eg_plan_impl *p) { return p->ar; }
+int plan_count(const eg_plan_impl *p) { return p->count; }
+int plan_bits(const eg_plan_impl *p) { return p->bits; }
+}  // namespace eg
+
 extern "C" {
 
 eg_status eg_plan_create(eg_arena *arena, int32_t count, const int32_t *part, const int64_t *w_scale,

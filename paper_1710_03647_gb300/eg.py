@@ -77,6 +77,18 @@ class eg_server_counters(ctypes.Structure):
 EG_SRV_FAIL_RESERVATIONS = 1
 
 
+class eg_tuning(ctypes.Structure):
+    _fields_ = [("local_windows", ctypes.c_int32), ("local_maxdeg", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("cap_certify", ctypes.c_int32),
+                ("certify_after", ctypes.c_int64), ("default_ms", ctypes.c_double), ("tuned_ms", ctypes.c_double),
+                ("solves", ctypes.c_int32), ("from_cache", ctypes.c_int32), ("key", ctypes.c_char * 96)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["key"] = self.key.decode()
+        return d
+
+
 class EGError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -106,6 +118,8 @@ SIGNATURES = {
     "eg_poll": (_I32, [_P, ctypes.c_uint64, _P, ctypes.POINTER(eg_stats)]),
     "eg_server_destroy": (_I32, [_P]),
     "eg_server_counters_get": (_I32, [_P, ctypes.POINTER(eg_server_counters)]),
+    "eg_autotune": (_I32, [_P, _I32, _I64, _I64, ctypes.c_char_p, _I32, ctypes.POINTER(eg_tuning)]),
+    "eg_plan_autotune": (_I32, [_P, ctypes.c_char_p, _I32, ctypes.POINTER(eg_tuning)]),
     "eg_server_set_option": (_I32, [_P, _I32, _I64]),
     "eg_last_error": (ctypes.c_char_p, []),
     "eg_version": (ctypes.c_char_p, []),
@@ -416,3 +430,19 @@ def eg_server_counters_get(server) -> dict:
 
 def eg_server_set_option(server, option: int, value: int) -> None:
     _check(load().eg_server_set_option(server, option, value))
+
+
+def eg_autotune(arena, credit_bits=0, w_scale=1, w_shift=0, cache_path=None, max_solves=0) -> dict:
+    """Tunes the arena's launch settings (see eg.h); returns the eg_tuning fields."""
+    t = eg_tuning()
+    path = cache_path.encode() if cache_path else None
+    _check(load().eg_autotune(arena, credit_bits, w_scale, w_shift, path, max_solves, ctypes.byref(t)))
+    return t.as_dict()
+
+
+def eg_plan_autotune(plan, cache_path=None, max_solves=0) -> dict:
+    t = eg_tuning()
+    path = cache_path.encode() if cache_path else None
+    handle = plan.handle if isinstance(plan, Plan) else plan
+    _check(load().eg_plan_autotune(handle, path, max_solves, ctypes.byref(t)))
+    return t.as_dict()

@@ -83,16 +83,19 @@ def test_missing_library_fails_loudly(tmp_path):
         eg._lib = saved
 
 
-def test_stats_layout_matches_header(tmp_path):
-    # the binding's eg_stats must have the C struct's size and field offsets
+@pytest.mark.parametrize("struct", [eg.eg_stats, eg.eg_tuning, eg.eg_server_counters],
+                         ids=lambda s: s.__name__)
+def test_struct_layout_matches_header(tmp_path, struct):
+    # each binding struct must have the C struct's size and field offsets
+    name = struct.__name__
     src = tmp_path / "layout.c"
-    fields = [f for f, _ in eg.eg_stats._fields_]
-    body = "\n".join(f'printf("{f} %zu\\n", offsetof(eg_stats, {f}));' for f in fields)
+    fields = [f for f, _ in struct._fields_]
+    body = "\n".join(f'printf("{f} %zu\\n", offsetof({name}, {f}));' for f in fields)
     src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "eg.h"\nint main(void) {\n'
-                   f'printf("size %zu\\n", sizeof(eg_stats));\n{body}\nreturn 0;\n}}\n')
+                   f'printf("size %zu\\n", sizeof({name}));\n{body}\nreturn 0;\n}}\n')
     exe = tmp_path / "layout"
     subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
     got = dict(line.split() for line in subprocess.check_output([str(exe)], text=True).splitlines())
-    assert int(got["size"]) == ctypes.sizeof(eg.eg_stats)
+    assert int(got["size"]) == ctypes.sizeof(struct)
     for f in fields:
-        assert int(got[f]) == getattr(eg.eg_stats, f).offset, f
+        assert int(got[f]) == getattr(struct, f).offset, f
