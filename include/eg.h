@@ -365,7 +365,11 @@ eg_status eg_plan_autotune(eg_plan *plan, const char *cache_path, int32_t max_so
  * solve has dropped its remaining work.  A game of at least 2^19 edges fills
  * the GPU alone and gains nothing from sharing it: it skips the pool and is
  * solved by eg_solve_credit's route between slices (its stats are that
- * solve's).  The result of every request equals eg_solve_credit on its arena
+ * solve's).  A request that finds the server idle -- nothing resident and no
+ * other request queued -- first gets that route's first attempt alone
+ * (EG_OPT_CERTIFY_AFTER rounds, or 8): with the device idle, sharing it
+ * gains nothing, and most games finish within it; a game it does not finish
+ * joins the pool as above.  The result of every request equals eg_solve_credit on its arena
  * alone (the games are disjoint in the pool; each has its own bound C and
  * weight map).  Results wait in pinned host buffers that the server reuses.
  * Do not solve an arena yourself while a request for it is pending.
@@ -391,14 +395,16 @@ eg_status eg_server_destroy(eg_server *server);
 
 /*
  * eg_server_counters_get -- the server's event counts since it was created:
- * requests submitted, admitted into the pool, solved alone because they fill
- * the GPU (solo), taken out of the pool to be solved alone by the certified
- * route (taken_out), completed (any status), admission attempts refused for
- * want of pool room (refused; the request stays queued and is retried after
- * the next slice), and slices of the resident solve run.
+ * requests submitted, admitted into the pool, solved alone by the single-game
+ * route (solo: the games that fill the GPU and the requests the idle route
+ * answered; idle_solo counts the latter), taken out of the pool to be solved
+ * alone by the certified route (taken_out), completed (any status),
+ * admission attempts refused for want of pool room (refused; the request
+ * stays queued and is retried after the next slice), and slices of the
+ * resident solve run.
  */
 typedef struct eg_server_counters {
-    int64_t submitted, admitted, solo, taken_out, completed, refused, slices;
+    int64_t submitted, admitted, solo, taken_out, completed, refused, slices, idle_solo;
 } eg_server_counters;
 eg_status eg_server_counters_get(eg_server *server, eg_server_counters *out);
 
@@ -408,9 +414,13 @@ eg_status eg_server_counters_get(eg_server *server, eg_server_counters *out);
  *     reservations of pool room at admission fail as if the pool were full,
  *     so the refusal and retry path of admission can be exercised on the
  *     host without exhausting device memory.
- * EG_ERR_INVALID for an unknown option or a negative value.
+ *   EG_SRV_IDLE_SOLO (default 1): a request that finds the server idle gets
+ *     the single-game route's first attempt alone before it joins the pool;
+ *     0 sends every request to the pool.
+ * EG_ERR_INVALID for an unknown option or a value out of range.
  */
 #define EG_SRV_FAIL_RESERVATIONS 1
+#define EG_SRV_IDLE_SOLO 2
 eg_status eg_server_set_option(eg_server *server, int32_t option, int64_t value);
 
 /* eg_last_error -- message of the calling thread's last failure ("" if none). */

@@ -118,8 +118,10 @@ namespace eg {
 // Implemented in eg_solve.cu
 eg_status compute_bound(eg_arena *a, long long scale, long long shift, long long *C, long long *wmax,
                         cudaStream_t s);
+// eg_solve_credit's route; with attempt_only > 0 only its first attempt (cap
+// C, that many rounds), which ends with EG_ERR_BUDGET if it does not finish.
 eg_status solve(eg_arena *a, int credit_bits, long long scale, long long shift, void *out, eg_stats *st,
-                cudaStream_t s, long long max_rounds);
+                cudaStream_t s, long long max_rounds, long long attempt_only = 0);
 eg_status free_state(StateBuffers &sb);
 
 // Resident solve (eg_solve.cu), used by the server: one int64 solve state

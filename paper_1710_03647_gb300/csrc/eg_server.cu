@@ -64,6 +64,7 @@ struct Request {
     long long vb = 0, eb = 0;
     long long C = 0;
     long long r_admit = 0;
+    bool tried_alone = false;  // took the idle route's short attempt already
     unsigned long long relax0 = 0, lifts0 = 0, pushes0 = 0, enq0 = 0;
     double dev_ms = 0;
 };
@@ -231,6 +232,7 @@ struct Server {
     Resident R;
     PinPool pins;  // result buffers
     long long fail_reservations = 0;  // test hook: reservations still to refuse
+    int idle_solo = 1;                // a lone request on an idle server gets a short attempt alone
     eg_server_counters ctr{};         // under mu
 };
 
@@ -354,6 +356,33 @@ static void solo(Server *S, Request *r, std::vector<Request *> &fin) {
     fin.push_back(r);
 }
 
+// The idle route: a request that found the server idle gets the single-game
+// route's first attempt alone (EG_OPT_CERTIFY_AFTER rounds, 8 if that is 0).
+// Returns true if that settled it (solved or failed), false if it needs more
+// rounds; then it goes to the pool like any other request.
+static bool idle_attempt(Server *S, Request *r, std::vector<Request *> &fin) {
+    r->tried_alone = true;
+    const long long rounds = r->ar->certify_after > 0 ? r->ar->certify_after : 8;
+    eg_stats st{};
+    eg_status rc = take_result(S->pins, r, (size_t)r->ar->n, r->credit_bits == 32 ? 4 : 8);
+    if (rc == EG_OK) rc = solve(r->ar, r->credit_bits, r->scale, r->shift, r->res, &st, S->stream, 0, rounds);
+    if (rc == EG_ERR_BUDGET) {
+        drop_result(S->pins, r);
+        return false;
+    }
+    r->status = rc;
+    if (rc == EG_OK) {
+        r->st = st;
+        std::lock_guard<std::mutex> lk(S->mu);
+        ++S->ctr.solo;
+        ++S->ctr.idle_solo;
+    } else {
+        drop_result(S->pins, r);
+    }
+    fin.push_back(r);
+    return true;
+}
+
 // Solves a slow resident game alone with certified trial caps, then retires
 // its slot (views with C < 0: the kernel drops its entries).
 static eg_status take_out(Server *S, Request *r, std::vector<Request *> &fin) {
@@ -470,7 +499,7 @@ static void worker_main(Server *S) {
     cudaSetDevice(S->device);
     std::vector<Request *> fin;
     for (;;) {
-        std::vector<Request *> admitted, alone;
+        std::vector<Request *> admitted, alone, idle;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             S->cv.wait(lk, [&] { return S->stop || !S->queue.empty() || S->nactive > 0 || !S->retiring.empty(); });
@@ -488,6 +517,15 @@ static void worker_main(Server *S) {
                     S->queue.pop_front();
                     ++S->ctr.solo;
                     alone.push_back(r);
+                    continue;
+                }
+                // the only request, and nothing resident: the device is idle, so
+                // a short attempt alone answers most games without the pool copy
+                // and the slice round trip
+                if (S->idle_solo && !r->tried_alone && S->nactive == 0 && S->retiring.empty() && admitted.empty() &&
+                    alone.empty() && idle.empty() && S->queue.size() == 1) {
+                    S->queue.pop_front();
+                    idle.push_back(r);
                     continue;
                 }
                 if (S->free_slots.empty()) break;
@@ -531,6 +569,15 @@ static void worker_main(Server *S) {
         for (Request *r : alone) {
             solo(S, r, fin);
             complete(S, fin);
+        }
+        for (Request *r : idle) {
+            if (idle_attempt(S, r, fin)) {
+                complete(S, fin);
+                continue;
+            }
+            // unfinished: back to the front of the queue, to join the pool
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->queue.push_front(r);
         }
         complete(S, fin);
         if (S->nactive == 0 && S->retiring.empty()) continue;
@@ -723,6 +770,15 @@ eg_status eg_server_set_option(eg_server *S, int32_t option, int64_t value) {
     case EG_SRV_FAIL_RESERVATIONS: {
         std::lock_guard<std::mutex> lk(S->mu);
         S->fail_reservations = value;
+        break;
+    }
+    case EG_SRV_IDLE_SOLO: {
+        if (value > 1) {
+            eg::set_error("EG_SRV_IDLE_SOLO takes 0 or 1");
+            return EG_ERR_INVALID;
+        }
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->idle_solo = (int)value;
         break;
     }
     default: eg::set_error("unknown server option %d", option); return EG_ERR_INVALID;

@@ -1270,6 +1270,7 @@ struct SolveMem {
     unsigned long long *aux = nullptr;
     bool fixed = false;     // laid over the allocation-free array
     bool in_place = false;  // sb's credit array is the caller's output buffer
+    long long attempt_only = 0;  // > 0: only a first attempt of this many rounds (EG_ERR_BUDGET if unfinished)
 };
 
 // The dual state and the trial bitmaps of an allocating solve.
@@ -1445,13 +1446,14 @@ static eg_status solve_route(eg_arena *ar, SolveMem &m, int bits, int credit_bit
     // With certification on, a first solve with cap C gets a short round
     // budget; only a game it does not finish goes through the trial caps.
     bool copied = m.in_place, attempt_out = false;
-    if (ar->cap_certify > 0 && ar->warm_start && ar->certify_after > 0 &&
-        (max_rounds == 0 || max_rounds > ar->certify_after)) {
+    if (m.attempt_only > 0 || (ar->cap_certify > 0 && ar->warm_start && ar->certify_after > 0 &&
+                               (max_rounds == 0 || max_rounds > ar->certify_after))) {
         // the credits are copied out right behind the attempt, before the
         // host learns whether it finished; the usual case then costs one
         // synchronisation, and a game that goes on overwrites them later
         if (m.fixed) sb.dirty = true;
-        const Launch L = launch_of(ar, 1, ar->certify_after);
+        const Launch L = m.attempt_only > 0 ? launch_of(ar, ar->warm_start, m.attempt_only)
+                                            : launch_of(ar, 1, ar->certify_after);
         rc = bits == 32 ? launch_solve<int>(ar, sb, WeightView{scale, shift, C}, s, L)
                         : launch_solve<long long>(ar, sb, WeightView{scale, shift, C}, s, L);
         if (rc != EG_OK) return rc;
@@ -1467,7 +1469,13 @@ static eg_status solve_route(eg_arena *ar, SolveMem &m, int bits, int credit_bit
             exact = copied = true;
         } else {
             sb.dirty = true;
-            if (dev == DEV_BUDGET) dev = DEV_OK;
+            if (dev == DEV_BUDGET && m.attempt_only == 0) dev = DEV_OK;
+        }
+        if (m.attempt_only > 0 && dev != DEV_OK) {
+            set_error(dev == DEV_BUDGET ? "no fixpoint within %lld rounds" : "a device-side wait exceeded its limit",
+                      m.attempt_only);
+            if (st) fill_stats(st, tot, C, tot.seeded, bits, dev == DEV_BUDGET ? EG_ERR_BUDGET : EG_ERR_TIMEOUT);
+            return dev == DEV_BUDGET ? EG_ERR_BUDGET : EG_ERR_TIMEOUT;
         }
     }
     bool trial_failed = false;
@@ -1532,7 +1540,7 @@ static eg_status solve_route(eg_arena *ar, SolveMem &m, int bits, int credit_bit
 }
 
 eg_status solve(eg_arena *ar, int credit_bits, long long scale, long long shift, void *out, eg_stats *st,
-                cudaStream_t s, long long max_rounds) {
+                cudaStream_t s, long long max_rounds, long long attempt_only) {
     if (credit_bits != 0 && credit_bits != 32 && credit_bits != 64) {
         set_error("credit_bits must be 0, 32 or 64");
         return EG_ERR_INVALID;
@@ -1554,6 +1562,7 @@ eg_status solve(eg_arena *ar, int credit_bits, long long scale, long long shift,
     if ((rc = ensure_state(ar, bits)) != EG_OK) return rc;
     SolveMem m;
     m.sb = bits == 32 ? &ar->st32 : &ar->st64;
+    m.attempt_only = attempt_only;
     return solve_route(ar, m, bits, credit_bits, scale, shift, C, wmax, out, st, s, max_rounds);
 }
 

@@ -68,13 +68,14 @@ class eg_stats(ctypes.Structure):
 
 class eg_server_counters(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("submitted", "admitted", "solo", "taken_out", "completed", "refused",
-                                               "slices")]
+                                               "slices", "idle_solo")]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 EG_SRV_FAIL_RESERVATIONS = 1
+EG_SRV_IDLE_SOLO = 2
 
 
 class eg_tuning(ctypes.Structure):

@@ -122,6 +122,7 @@ def test_admission_refuses_then_retries():
     arenas = [eg.Arena(g) for g in gs]
     server = eg.eg_server_create(1 << 30, 4)
     try:
+        eg.eg_server_set_option(server, eg.EG_SRV_IDLE_SOLO, 0)  # every request goes to the pool
         eg.eg_server_set_option(server, eg.EG_SRV_FAIL_RESERVATIONS, 3)
         tickets = [eg.eg_submit(server, a.handle, 0, 1, 0) for a in arenas]
         for g, t in zip(gs, tickets):

@@ -234,3 +234,39 @@ def test_large_games_are_solved_alone_between_slices():
         eg.eg_server_destroy(server)
         for a in arenas:
             a.close()
+
+
+def test_idle_server_answers_a_lone_request_alone():
+    # a request that finds the server idle gets a short attempt by the
+    # single-game route; a game that attempt does not finish joins the pool
+    easy = gen.rmat_game(12, 8, seed=9)
+    slow = gen.grid_game(64, 64, seed=1)
+    a_easy, a_slow = eg.Arena(easy), eg.Arena(slow)
+    a_slow.tune(cap_certify=0)  # stays in the resident solve once admitted
+    want_easy = alone(a_easy.handle, 0, 1, 0, easy.n)
+    want_slow = alone(a_slow.handle, 64, 1, 0, slow.n)
+    server = eg.eg_server_create(1 << 30, 4)
+    try:
+        out = np.empty(easy.n, dtype=np.int64)
+        rc, st = wait(server, eg.eg_submit(server, a_easy.handle, 0, 1, 0), out)
+        assert rc == eg.EG_OK
+        np.testing.assert_array_equal(out, want_easy)
+        c = eg.eg_server_counters_get(server)
+        assert c["idle_solo"] == 1 and c["admitted"] == 0
+        out = np.empty(slow.n, dtype=np.int64)
+        rc, st = wait(server, eg.eg_submit(server, a_slow.handle, 64, 1, 0), out, timeout=120)
+        assert rc == eg.EG_OK
+        np.testing.assert_array_equal(out, want_slow)
+        c = eg.eg_server_counters_get(server)
+        assert c["idle_solo"] == 1 and c["admitted"] == 1 and c["completed"] == 2
+        eg.eg_server_set_option(server, eg.EG_SRV_IDLE_SOLO, 0)
+        out = np.empty(easy.n, dtype=np.int64)
+        rc, _ = wait(server, eg.eg_submit(server, a_easy.handle, 0, 1, 0), out)
+        assert rc == eg.EG_OK and eg.eg_server_counters_get(server)["admitted"] == 2
+        np.testing.assert_array_equal(out, want_easy)
+        with pytest.raises(eg.EGError):
+            eg.eg_server_set_option(server, eg.EG_SRV_IDLE_SOLO, 2)
+    finally:
+        eg.eg_server_destroy(server)
+        a_easy.close()
+        a_slow.close()
