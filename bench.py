@@ -264,7 +264,7 @@ def traffic_record(name):
     return rec.get("dram_bytes_per_launch")
 
 
-def rmat_context(eg, gen, torch, dev, stream, flush, plain_start=True, tune=True):
+def rmat_context(eg, gen, torch, dev, stream, flush, plain_start=True, tune=True, scc=True):
     """Config 2 (R-MAT scale 20, int32): time to the fixpoint, relaxations/s
     and the fixpoint kernel against HBM, beside the oracle's stored time on
     the same game; optionally the paper's f = 0 start."""
@@ -315,6 +315,32 @@ def rmat_context(eg, gen, torch, dev, stream, flush, plain_start=True, tune=True
         pd = pst.as_dict()
         out_d["plain"] = {"time_to_fixpoint_ms": pd["ms"], "relaxations": pd["relaxations"], "rounds": pd["rounds"],
                           "note": "same solver, warm start and certified trials off (f = 0 start as in the paper)"}
+    if scc:
+        # SCC-ordered solving (levels of the condensation in turn): the
+        # default warm start, and the paper's f = 0 start
+        t0 = time.perf_counter()
+        info = eg.eg_scc_info(arena.handle)
+        info["condensation_ms"] = (time.perf_counter() - t0) * 1e3
+        arena.tune(scc_order=1)
+        sms = []
+        for _ in range(5):
+            b, e = ev_pair()
+            b.record(stream)
+            _, sst = eg.eg_solve_credit(arena.handle, bits, 1, 0, out, stream=stream.cuda_stream)
+            e.record(stream)
+            torch.cuda.synchronize()
+            sms.append(b.elapsed_time(e))
+        info["warm_time_to_fixpoint_ms"] = statistics.median(sms)
+        info["warm_relaxations"] = sst.relaxations
+        if plain_start:
+            arena.tune(warm_start=0)
+            _, pst = eg.eg_solve_credit(arena.handle, bits, 1, 0, out, stream=stream.cuda_stream)
+            arena.tune(warm_start=1)
+            info["plain_time_to_fixpoint_ms"] = pst.ms
+            info["plain_relaxations"] = pst.relaxations
+            info["plain_rounds"] = pst.rounds
+        arena.tune(scc_order=0)
+        out_d["scc_ordered"] = info
     return arena, a, out_d
 
 
@@ -326,6 +352,9 @@ def batch_games(eg, gen, torch, dev, stream, count, tune=True):
     n, row_ptr, col, w, owner_bits, part_ptr = eg.pack_games(games)
     h = eg.eg_create(n, int(row_ptr[-1]), row_ptr, col, w, owner_bits=owner_bits)
     eg.eg_set_parts(h, part_ptr)
+    t0 = time.perf_counter()
+    scc = eg.eg_scc_info(h)  # the condensation of all games: how much SCC ordering could order
+    scc["condensation_ms"] = (time.perf_counter() - t0) * 1e3
     plan = eg.Plan(h, count)
     bout = torch.empty(plan.total, dtype=torch.int64, device=dev)
     plan.run(bout, stream=stream.cuda_stream)
@@ -374,7 +403,7 @@ def batch_games(eg, gen, torch, dev, stream, count, tune=True):
             "batched_ms": bmed, "batched_games_per_s": count / (bmed * 1e-3), "batched_relaxations": bst.relaxations,
             "per_game_total_ms": total, "per_game_games_per_s": count / (total * 1e-3),
             "per_game_p50_ms": lat[len(lat) // 2], "per_game_p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-            "batched_equals_per_game": bool(same), "plan_tuning": tuning,
+            "batched_equals_per_game": bool(same), "plan_tuning": tuning, "condensation": scc,
             "note": "batched: one plan (one persistent launch, CUDA graph replay) over a packed arena; latency of "
                     "every game in the batch = the batch time"}
 
@@ -506,6 +535,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched threshold-query comparison")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     ap.add_argument("--no-tune", action="store_true", help="time the default settings (no eg_autotune)")
+    ap.add_argument("--no-scc", action="store_true", help="skip the SCC-ordered context solves")
     ap.add_argument("--batch-games", type=int, default=4096, help="games in the batched-vs-per-game comparison "
                     "(4096 = the full workload; 0 skips it)")
     ap.add_argument("--serve-requests", type=int, default=512, help="requests per arrival rate (0 skips serving)")
@@ -631,7 +661,7 @@ def main():
     rarena = None
     if single and not args.no_context:
         rarena, ra, context = rmat_context(eg, gen, torch, dev, stream, flush, plain_start=not args.no_plain,
-                                           tune=not args.no_tune)
+                                           tune=not args.no_tune, scc=not args.no_scc)
 
     # 256 mean-payoff threshold queries on the R-MAT arena (w' = 256 w - k W,
     # k = -128..127, W = 100): one batched launch vs one solve per query

@@ -60,6 +60,7 @@ typedef struct eg_server eg_server;
 #define EG_PHASE_DUAL 1        /* certified trial: lift of the dual game */
 #define EG_PHASE_CAPPED 2      /* certified trial: lift of the game with cap B */
 #define EG_PHASE_FINAL 3       /* lift with cap C from the trials' proven TOP starts */
+#define EG_PHASE_LEVEL 4       /* SCC-ordered solve: lift of one topological level */
 
 /* Counters of one solve.  relaxations counts evaluations of f(u) (-) w over
  * edges (pulls of player-0 lifts plus pushes to predecessors); lifts counts
@@ -223,6 +224,13 @@ eg_status eg_strategy(eg_arena *arena, int32_t credit_bits, int64_t w_scale, int
  *     device stays usable and the arena can be solved again.  A very small
  *     limit makes ordinary waits run out; that is how the timeout path is
  *     tested.
+ *   EG_OPT_SCC_ORDER (default 0): 1 solves by strongly connected components
+ *     (the closing remark of Sec. 6): the components' topological levels
+ *     (eg_scc_info) are lifted in turn, lowest first, each with cap C and
+ *     the lower levels final, as the paper's lifting does (no certified
+ *     trials).  A condensation of a single level (one component, as a
+ *     road-like grid has) takes the default route instead.
+ *     eg_solve_credit_noalloc ignores the option.
  *
  * EG_ERR_INVALID for an unknown option or a value out of range.
  */
@@ -235,7 +243,25 @@ eg_status eg_strategy(eg_arena *arena, int32_t credit_bits, int64_t w_scale, int
 #define EG_OPT_CERTIFY_AFTER 7
 #define EG_OPT_BLOCKS_PER_SM 8
 #define EG_OPT_WAIT_LIMIT_US 9
+#define EG_OPT_SCC_ORDER 10
 eg_status eg_set_option(eg_arena *arena, int32_t option, int64_t value);
+
+/*
+ * eg_scc_info / eg_scc_levels -- the strongly connected components of the
+ * arena's graph (Sec. 2) and their topological levels: a component from which
+ * no edge leaves has level 0, any other one more than the highest level its
+ * edges reach, so a vertex's least-EPM value depends only on vertices of its
+ * level or lower.  Computed on the device on first use (trimming, max-label
+ * colouring, backward closure; Kahn's rounds for the levels, of which at
+ * most 4096 are kept: components beyond share the last one) and kept with
+ * the arena.  eg_scc_info gives the number of components, of levels and of
+ * kernel passes the computation took (any pointer may be NULL);
+ * eg_scc_levels copies the level and the component (named by its largest
+ * vertex id) of every vertex to int32[n] host or device arrays (either may
+ * be NULL).  Both allocate device memory on first use and are synchronous.
+ */
+eg_status eg_scc_info(eg_arena *arena, int64_t *components, int64_t *levels, int64_t *passes);
+eg_status eg_scc_levels(eg_arena *arena, int32_t *level_out, int32_t *component_out);
 
 /*
  * eg_set_parts -- declare the arena a disjoint union of `parts` games: game k

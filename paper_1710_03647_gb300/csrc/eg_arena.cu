@@ -309,6 +309,8 @@ static eg_status destroy(eg_arena *a) {
     free_state(a->st32);
     free_state(a->st64);
     free_state(a->st_dual);
+    if (a->scc_level) cudaFree(a->scc_level);
+    if (a->scc_comp) cudaFree(a->scc_comp);
     if (a->block) cudaFree(a->block);
     if (a->cert_block) cudaFree(a->cert_block);
     if (a->ev0) cudaEventDestroy(a->ev0);
@@ -683,6 +685,13 @@ eg_status eg_set_option(eg_arena *arena, int32_t option, int64_t value) {
     case EG_OPT_CAP_CERTIFY: arena->cap_certify = (int)value; break;
     case EG_OPT_CERTIFY_AFTER: arena->certify_after = value; break;
     case EG_OPT_BLOCKS_PER_SM: arena->blocks_per_sm = (int)value; break;
+    case EG_OPT_SCC_ORDER:
+        if (value > 1) {
+            eg::set_error("EG_OPT_SCC_ORDER takes 0 or 1");
+            return EG_ERR_INVALID;
+        }
+        arena->scc_order = (int)value;
+        break;
     case EG_OPT_WAIT_LIMIT_US:
         if (value < 1) {
             eg::set_error("EG_OPT_WAIT_LIMIT_US takes at least 1");
@@ -698,6 +707,39 @@ eg_status eg_set_option(eg_arena *arena, int32_t option, int64_t value) {
         arena->use_graph = (int)value;
         break;
     default: eg::set_error("unknown option %d", option); return EG_ERR_INVALID;
+    }
+    return EG_OK;
+}
+
+eg_status eg_scc_info(eg_arena *arena, int64_t *components, int64_t *levels, int64_t *passes) {
+    eg::clear_error();
+    if (!arena) {
+        eg::set_error("arena is NULL");
+        return EG_ERR_INVALID;
+    }
+    eg_status rc = eg::scc_levels(arena, 0);
+    if (rc != EG_OK) return rc;
+    if (components) *components = arena->scc_count;
+    if (levels) *levels = arena->scc_nlevels;
+    if (passes) *passes = arena->scc_passes;
+    return EG_OK;
+}
+
+eg_status eg_scc_levels(eg_arena *arena, int32_t *level_out, int32_t *component_out) {
+    eg::clear_error();
+    if (!arena || (!level_out && !component_out)) {
+        eg::set_error("need an arena and an output");
+        return EG_ERR_INVALID;
+    }
+    eg_status rc = eg::scc_levels(arena, 0);
+    if (rc != EG_OK) return rc;
+    cudaError_t e = cudaSuccess;
+    if (level_out) e = cudaMemcpy(level_out, arena->scc_level, (size_t)arena->n * 4, cudaMemcpyDefault);
+    if (e == cudaSuccess && component_out)
+        e = cudaMemcpy(component_out, arena->scc_comp, (size_t)arena->n * 4, cudaMemcpyDefault);
+    if (e != cudaSuccess) {
+        eg::set_error("copy of the condensation failed: %s", cudaGetErrorString(e));
+        return EG_ERR_CUDA;
     }
     return EG_OK;
 }

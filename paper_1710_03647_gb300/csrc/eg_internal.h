@@ -106,6 +106,10 @@ struct eg_arena {
     int cap_certify = 4;              // first trial cap of the certified solve, in units of max|w'| (0: off)
     long long certify_after = 64;     // rounds of a first solve with cap C before the trial caps (0: none); eg_create sets the default
     int blocks_per_sm = 0;            // resident blocks per SM of the fixpoint kernel (0: as many as fit)
+    int scc_order = 0;                // solve by the topological levels of the strongly connected components
+    int *scc_level = nullptr;         // condensation (computed on first use): level of each vertex,
+    int *scc_comp = nullptr;          //   representative of its component,
+    int scc_nlevels = 0, scc_count = 0, scc_passes = 0;  //   levels, components, kernel passes taken
     unsigned long long wait_limit_ns = 5000000000ull;  // limit of each grid-barrier wait
     void *cert_block = nullptr;       // device memory of the certified solve:
     unsigned long long *aux = nullptr;  //   counters (4 words)
@@ -123,6 +127,9 @@ eg_status compute_bound(eg_arena *a, long long scale, long long shift, long long
 eg_status solve(eg_arena *a, int credit_bits, long long scale, long long shift, void *out, eg_stats *st,
                 cudaStream_t s, long long max_rounds, long long attempt_only = 0);
 eg_status free_state(StateBuffers &sb);
+// The strongly connected components and their topological levels (eg_scc.cu),
+// computed once per arena.
+eg_status scc_levels(eg_arena *a, cudaStream_t s);
 
 // Resident solve (eg_solve.cu), used by the server: one int64 solve state
 // over a pool of `cap` credits that holds up to `slots` games at a time.

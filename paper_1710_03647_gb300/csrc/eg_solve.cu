@@ -116,6 +116,8 @@ struct Args {
     int local_windows;  // per-warp budget of local windows per round (0: no chaining)
     int local_maxdeg;   // largest degree a vertex may have to be chained locally
     unsigned long long wait_ns;  // limit of each grid-barrier wait
+    const int *level;  // SCC-ordered solves: topological level of each vertex (or null)
+    int cur_level;     // the level being solved; predecessors above it are left for later
 };
 
 // One instance's view of the arena, carried per list entry.  A negative C
@@ -355,6 +357,50 @@ __global__ void __launch_bounds__(THREADS) k_init(Args<T> a, int g0, int g1, int
     }
 }
 
+// First lift of the vertices of one topological level of an SCC-ordered
+// solve: the lift over all successors with the current credits (the lower
+// levels are final, this level's vertices start at 0 or, warm-started, at
+// TOP); a vertex whose credit is positive joins the push list of round 0.
+// Reads of other vertices of the level may see their old or new credit:
+// both are at or below the least fixpoint.
+template <typename T>
+__global__ void __launch_bounds__(THREADS) k_init_level(Args<T> a, int level) {
+    const DevArena &A = a.A;
+    const int nthreads = gridDim.x * blockDim.x;
+    const WeightView &W = a.W;
+    for (int base = blockIdx.x * blockDim.x; base < A.n; base += nthreads) {
+        const int v = base + threadIdx.x;
+        bool want = false;
+        int work = 0;
+        if (v < A.n && __ldg(a.level + v) == level) {
+            const bool p1 = ((__ldg(A.owner_bits + (v >> 5)) >> (v & 31)) & 1u) ^ a.inv;
+            T cur = ld_cg(a.f + v);
+            if (cur != Cred<T>::TOP) {
+                T g = p1 ? T(0) : Cred<T>::TOP;
+                for (int e = __ldg(A.row_ptr + v); e < __ldg(A.row_ptr + v + 1); ++e) {
+                    const T t = ominus<T>(ld_cg(a.f + __ldg(A.col + e)), wmap(__ldg(A.w + e), W), W.C);
+                    g = p1 ? max(g, t) : min(g, t);
+                }
+                if (g > cur) {
+                    atomicMax(a.f + v, g);
+                    cur = g;
+                }
+            }
+            work = __ldg(A.rrow_ptr + v + 1) - __ldg(A.rrow_ptr + v);
+            want = cur > T(0) && work > 0;
+        }
+        warp_append(want, (unsigned)v, work, &a.ctrl->push_ctr[0], a.push_items[0], a.push_offs[0]);
+    }
+}
+
+// Credits of an SCC-ordered solve before its first level: TOP on the warm
+// start's vertices, else 0.
+template <typename T>
+__global__ void k_level_start(T *f, int n, const unsigned *seed_bits) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+        f[v] = seed_bits && ((seed_bits[v >> 5] >> (v & 31)) & 1u) ? Cred<T>::TOP : T(0);
+}
+
 // Per-instance bound C = M_G and max |w'| of every instance (one credit per
 // thread, from the weight extremes of its arena vertex; a warp whose credits
 // all belong to one instance adds them with one atomic).
@@ -584,7 +630,8 @@ __device__ __forceinline__ void push_edges(const Args<T> &a, int r, int beg, int
             const unsigned pr = __ldg(a.A.rcol + e);
             const int pa = (int)(pr & 0x7fffffffu);
             p = pa + wj.delta;
-            const bool fz = a.frozen && ((__ldg(a.frozen + (p >> 5)) >> (p & 31)) & 1u);
+            const bool fz = (a.frozen && ((__ldg(a.frozen + (p >> 5)) >> (p & 31)) & 1u)) ||
+                            (a.level && __ldg(a.level + p) > a.cur_level);
             const T t = ominus<T>(vj, wmapv(__ldg(a.A.rw + e), wj), wj.C);
             if (!fz && t > ld_cg(a.f + p)) {
                 if (((pr & P1_FLAG) != 0) != (a.inv != 0)) {
@@ -993,6 +1040,8 @@ struct Launch {
     int blocks_per_sm = 0;   // resident blocks per SM of the fixpoint kernel (0: as many as fit)
     unsigned long long wait_ns = BARRIER_LIMIT_NS;
     const unsigned *frozen = nullptr;  // vertices held at 0 (dual lifts of the certified trials)
+    const int *level = nullptr;        // SCC-ordered solves: level of each vertex
+    int cur_level = 0;                 //   and the level this launch solves (0 first)
 };
 
 // The arena's launch settings with the given warm start and round budget.
@@ -1046,8 +1095,11 @@ static eg_status enqueue_solve(const DevArena &A, const WeightView &W, const Ins
     a.wait_ns = L.wait_ns;
     a.inv = L.inv;
     a.frozen = L.frozen;
+    a.level = L.level;
+    a.cur_level = L.cur_level;
     a.seed_bits = nullptr;
-    if (L.warm_start || L.preseeded) {
+    const bool first = !L.level || L.cur_level == 0;  // an SCC-ordered solve seeds once, at level 0
+    if (first && (L.warm_start || L.preseeded)) {
         if (!L.preseeded) EG_CUDA_TRY(cudaMemsetAsync(sb.d.seed_bits, 0, ((size_t)nf + 31) / 32 * 4, s));
         if (L.warm_start) {
             const int sblocks = (int)std::min<long long>((nf + 7) / 8, (long long)sms * 32);
@@ -1058,7 +1110,13 @@ static eg_status enqueue_solve(const DevArena &A, const WeightView &W, const Ins
         a.seed_bits = sb.d.seed_bits;
     }
     const int init_blocks = (int)std::min<long long>((nf + THREADS - 1) / THREADS, (long long)sms * 16);
-    k_init<MULTI, T><<<init_blocks, THREADS, 0, s>>>(a, 0, (int)nf, 0, 0);
+    if (L.level) {
+        if (first)
+            k_level_start<T><<<init_blocks, THREADS, 0, s>>>(a.f, (int)nf, a.seed_bits);
+        k_init_level<T><<<init_blocks, THREADS, 0, s>>>(a, L.cur_level);
+    } else {
+        k_init<MULTI, T><<<init_blocks, THREADS, 0, s>>>(a, 0, (int)nf, 0, 0);
+    }
     EG_CUDA_TRY(cudaGetLastError());
 
     static int per_sm_cache[64] = {0};  // resident blocks per SM, per device
@@ -1219,7 +1277,7 @@ static void add_launch(Totals &t, const Ctrl *hc, double ms, double kms, int kin
     t.pushes += (long long)hc->pushes;
     t.relax += (long long)hc->relax;
     t.enqueues += (long long)hc->enqueues;
-    t.seeded = (long long)hc->seeded;
+    t.seeded = std::max(t.seeded, (long long)hc->seeded);
     t.ms += ms;
     t.kms += kms;
     t.phases.push_back(PhaseRec{kind, cap, (long long)hc->rounds, (long long)hc->relax, kms});
@@ -1443,6 +1501,35 @@ static eg_status solve_route(eg_arena *ar, SolveMem &m, int bits, int credit_bit
     int dev = DEV_OK;
     bool exact = false, seeded = false;
     long long nproven = 0;
+    // SCC-ordered solving: the levels of the condensation in turn, lowest
+    // first, each a lift with cap C over its own vertices (the allocation-free
+    // route has no room for the condensation and ignores the option)
+    if (ar->scc_order && !m.fixed && m.attempt_only == 0 && (rc = scc_levels(ar, s)) != EG_OK) return rc;
+    // a condensation of one level (one component, as on road-like grids)
+    // orders nothing: such a game takes the default route with its trials
+    if (ar->scc_order && !m.fixed && m.attempt_only == 0 && ar->scc_nlevels > 1) {
+        for (int l = 0; l < ar->scc_nlevels && dev == DEV_OK; ++l) {
+            Launch L = launch_of(ar, ar->warm_start, max_rounds);
+            L.level = ar->scc_level;
+            L.cur_level = l;
+            rc = bits == 32 ? run_phase<int>(ar, m, sb, WeightView{scale, shift, C}, L, s, tot, EG_PHASE_LEVEL, dev)
+                            : run_phase<long long>(ar, m, sb, WeightView{scale, shift, C}, L, s, tot, EG_PHASE_LEVEL,
+                                                   dev);
+            if (rc != EG_OK) return rc;
+        }
+        if (!m.in_place && (rc = enqueue_output(ar, sb, bits, credit_bits, out, s)) != EG_OK) return rc;
+        EG_CUDA_TRY(cudaStreamSynchronize(s));
+        eg_status result = EG_OK;
+        if (dev == DEV_TIMEOUT) {
+            set_error("a device-side wait exceeded its limit");
+            result = EG_ERR_TIMEOUT;
+        } else if (dev == DEV_BUDGET) {
+            set_error("round budget of %lld exhausted", max_rounds);
+            result = EG_ERR_BUDGET;
+        }
+        if (st) fill_stats(st, tot, C, tot.seeded, bits, result);
+        return result;
+    }
     // With certification on, a first solve with cap C gets a short round
     // budget; only a game it does not finish goes through the trial caps.
     bool copied = m.in_place, attempt_out = false;
@@ -2213,6 +2300,8 @@ static Args<long long> resident_args(const Resident &R) {
     a.local_windows = R.local_windows;
     a.local_maxdeg = R.local_maxdeg;
     a.wait_ns = BARRIER_LIMIT_NS;
+    a.level = nullptr;
+    a.cur_level = 0;
     return a;
 }
 

@@ -41,7 +41,8 @@ EG_PHASE_ATTEMPT = 0
 EG_PHASE_DUAL = 1
 EG_PHASE_CAPPED = 2
 EG_PHASE_FINAL = 3
-PHASE_NAMES = {0: "attempt", 1: "dual", 2: "capped", 3: "final"}
+EG_PHASE_LEVEL = 4
+PHASE_NAMES = {0: "attempt", 1: "dual", 2: "capped", 3: "final", 4: "level"}
 
 
 class eg_stats(ctypes.Structure):
@@ -119,6 +120,8 @@ SIGNATURES = {
     "eg_poll": (_I32, [_P, ctypes.c_uint64, _P, ctypes.POINTER(eg_stats)]),
     "eg_server_destroy": (_I32, [_P]),
     "eg_server_counters_get": (_I32, [_P, ctypes.POINTER(eg_server_counters)]),
+    "eg_scc_info": (_I32, [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)]),
+    "eg_scc_levels": (_I32, [_P, _P, _P]),
     "eg_autotune": (_I32, [_P, _I32, _I64, _I64, ctypes.c_char_p, _I32, ctypes.POINTER(eg_tuning)]),
     "eg_plan_autotune": (_I32, [_P, ctypes.c_char_p, _I32, ctypes.POINTER(eg_tuning)]),
     "eg_server_set_option": (_I32, [_P, _I32, _I64]),
@@ -202,6 +205,7 @@ EG_OPT_CAP_CERTIFY = 6
 EG_OPT_CERTIFY_AFTER = 7
 EG_OPT_BLOCKS_PER_SM = 8
 EG_OPT_WAIT_LIMIT_US = 9
+EG_OPT_SCC_ORDER = 10
 
 
 def eg_solve_credit_noalloc(arena, credit_bits, w_scale, w_shift, credits_out, stream=None, max_rounds=0,
@@ -277,11 +281,12 @@ class Arena:
         return out, st
 
     def tune(self, local_windows=None, local_maxdeg=None, warm_start=None, seed_max_pairs=None, cap_certify=None,
-             certify_after=None, blocks_per_sm=None, wait_limit_us=None):
+             certify_after=None, blocks_per_sm=None, wait_limit_us=None, scc_order=None):
         for opt, val in ((EG_OPT_LOCAL_WINDOWS, local_windows), (EG_OPT_LOCAL_MAXDEG, local_maxdeg),
                          (EG_OPT_WARM_START, warm_start), (EG_OPT_SEED_MAX_PAIRS, seed_max_pairs),
                          (EG_OPT_CAP_CERTIFY, cap_certify), (EG_OPT_CERTIFY_AFTER, certify_after),
-                         (EG_OPT_BLOCKS_PER_SM, blocks_per_sm), (EG_OPT_WAIT_LIMIT_US, wait_limit_us)):
+                         (EG_OPT_BLOCKS_PER_SM, blocks_per_sm), (EG_OPT_WAIT_LIMIT_US, wait_limit_us),
+                         (EG_OPT_SCC_ORDER, scc_order)):
             if val is not None:
                 eg_set_option(self.handle, opt, int(val))
 
@@ -447,3 +452,18 @@ def eg_plan_autotune(plan, cache_path=None, max_solves=0) -> dict:
     handle = plan.handle if isinstance(plan, Plan) else plan
     _check(load().eg_plan_autotune(handle, path, max_solves, ctypes.byref(t)))
     return t.as_dict()
+
+
+def eg_scc_info(arena) -> dict:
+    """Components, topological levels and kernel passes of the arena's condensation."""
+    c, l, p = _I64(), _I64(), _I64()
+    _check(load().eg_scc_info(arena, ctypes.byref(c), ctypes.byref(l), ctypes.byref(p)))
+    return {"components": c.value, "levels": l.value, "passes": p.value}
+
+
+def eg_scc_levels(arena, n):
+    """(level, component) int32 arrays of the arena's n vertices."""
+    level = np.empty(n, dtype=np.int32)
+    comp = np.empty(n, dtype=np.int32)
+    _check(load().eg_scc_levels(arena, level.ctypes.data, comp.ctypes.data))
+    return level, comp
