@@ -205,14 +205,19 @@ eg_status eg_strategy(eg_arena *arena, int32_t credit_bits, int64_t w_scale, int
  *     finite or proven lost, every finite credit is at most B, and a cap at or
  *     above the largest finite credit gives the same least fixpoint as C
  *     (Sec. 3.1): the capped result is exact.  Trial k uses
- *     B = value * max|w'| * 4^k and K = 8^(k+1) (at most n + 1), k < 6; if no
- *     trial is exact the solve ends with cap C from the proven TOP starts.
+ *     B = value * max|w'| * 4^k and K = EG_OPT_DUAL_K * 8^k (at most n + 1),
+ *     k < 6; if no trial is exact the solve ends with cap C from the proven
+ *     TOP starts.
  *     This turns the pseudo-polynomial climb of player-1 vertices to C into
  *     climbs to B.  0 turns it off.  max_rounds bounds each fixpoint launch.
  *   EG_OPT_CERTIFY_AFTER (default 8): with certification on, a plain solve
  *     (cap C, warm start) runs first with this round budget, and the trials
  *     start only if it does not reach the fixpoint; 0 starts with the trials.
  *     The value changes the time to the fixpoint, never the result.
+ *   EG_OPT_DUAL_K (default 4): K of the first trial's dual lift.  A larger K
+ *     proves player-1 wins on longer cycles of small weight in the first
+ *     trial; a smaller one keeps the dual credits, and so the dual lift's
+ *     climbs, short.
  *   EG_OPT_BLOCKS_PER_SM (default 0): resident blocks per SM of the
  *     persistent fixpoint kernel; 0 takes as many as fit, a larger value is
  *     clamped to what fits.  Fewer blocks make the grid barrier cheaper and
@@ -244,6 +249,7 @@ eg_status eg_strategy(eg_arena *arena, int32_t credit_bits, int64_t w_scale, int
 #define EG_OPT_BLOCKS_PER_SM 8
 #define EG_OPT_WAIT_LIMIT_US 9
 #define EG_OPT_SCC_ORDER 10
+#define EG_OPT_DUAL_K 11
 eg_status eg_set_option(eg_arena *arena, int32_t option, int64_t value);
 
 /*
@@ -340,7 +346,8 @@ eg_status eg_solve_credit_noalloc(eg_arena *arena, int32_t credit_bits, int64_t 
  * analysis of the input).  The settings of eg_set_option that change only
  * how fast the least fixpoint is reached -- EG_OPT_LOCAL_WINDOWS,
  * EG_OPT_LOCAL_MAXDEG, EG_OPT_BLOCKS_PER_SM and, when the certified trials
- * run, EG_OPT_CAP_CERTIFY and EG_OPT_CERTIFY_AFTER -- are chosen by timing
+ * run, EG_OPT_CAP_CERTIFY, EG_OPT_DUAL_K and EG_OPT_CERTIFY_AFTER -- are
+ * chosen by timing
  * real solves (every one of them exact) in a coordinate search that starts
  * from the arena's current settings; a candidate replaces the best so far
  * only if it is more than 3% faster.  The chosen settings are set on the
@@ -361,6 +368,7 @@ eg_status eg_solve_credit_noalloc(eg_arena *arena, int32_t credit_bits, int64_t 
 typedef struct eg_tuning {
     int32_t local_windows, local_maxdeg, blocks_per_sm, cap_certify;
     int64_t certify_after;
+    int32_t dual_k, reserved;
     double default_ms;   /* time to the fixpoint with the settings the search started from (-1: cached) */
     double tuned_ms;     /* with the chosen settings (the cached figure when from_cache) */
     int32_t solves;      /* runs timed by this call */

@@ -685,6 +685,13 @@ eg_status eg_set_option(eg_arena *arena, int32_t option, int64_t value) {
     case EG_OPT_CAP_CERTIFY: arena->cap_certify = (int)value; break;
     case EG_OPT_CERTIFY_AFTER: arena->certify_after = value; break;
     case EG_OPT_BLOCKS_PER_SM: arena->blocks_per_sm = (int)value; break;
+    case EG_OPT_DUAL_K:
+        if (value < 1) {
+            eg::set_error("EG_OPT_DUAL_K takes at least 1");
+            return EG_ERR_INVALID;
+        }
+        arena->dual_k = (int)value;
+        break;
     case EG_OPT_SCC_ORDER:
         if (value > 1) {
             eg::set_error("EG_OPT_SCC_ORDER takes 0 or 1");

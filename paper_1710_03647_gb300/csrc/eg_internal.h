@@ -104,6 +104,7 @@ struct eg_arena {
     long long seed_max_pairs = 4096;
     int use_graph = 1;                // batched solves replay a captured graph
     int cap_certify = 4;              // first trial cap of the certified solve, in units of max|w'| (0: off)
+    int dual_k = 4;                   // weight multiplier K of the first trial's dual lift
     long long certify_after = 64;     // rounds of a first solve with cap C before the trial caps (0: none); eg_create sets the default
     int blocks_per_sm = 0;            // resident blocks per SM of the fixpoint kernel (0: as many as fit)
     int scc_order = 0;                // solve by the topological levels of the strongly connected components

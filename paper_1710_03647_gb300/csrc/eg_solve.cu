@@ -630,17 +630,23 @@ __device__ __forceinline__ void push_edges(const Args<T> &a, int r, int beg, int
             const unsigned pr = __ldg(a.A.rcol + e);
             const int pa = (int)(pr & 0x7fffffffu);
             p = pa + wj.delta;
+            const bool p1 = ((pr & P1_FLAG) != 0) != (a.inv != 0);
+            // the row the predecessor would be queued with (in-edges for a
+            // player-1 rise, out-edges for a player-0 lift), loaded beside
+            // its credit rather than after the test
+            const int *rp = p1 ? a.A.rrow_ptr : a.A.row_ptr;
+            const int rb = __ldg(rp + pa), re = __ldg(rp + pa + 1);
             const bool fz = (a.frozen && ((__ldg(a.frozen + (p >> 5)) >> (p & 31)) & 1u)) ||
                             (a.level && __ldg(a.level + p) > a.cur_level);
             const T t = ominus<T>(vj, wmapv(__ldg(a.A.rw + e), wj), wj.C);
             if (!fz && t > ld_cg(a.f + p)) {
-                if (((pr & P1_FLAG) != 0) != (a.inv != 0)) {
+                if (p1) {
                     if (t > atomicMax(a.f + p, t)) {
-                        work = __ldg(a.A.rrow_ptr + pa + 1) - __ldg(a.A.rrow_ptr + pa);
+                        work = re - rb;
                         if (work > 0) need = NEED_PUSH;
                     }
                 } else {
-                    work = __ldg(a.A.row_ptr + pa + 1) - __ldg(a.A.row_ptr + pa);
+                    work = re - rb;
                     need = NEED_PULL;
                 }
             }
@@ -677,10 +683,20 @@ __device__ void drain_local(const Args<T> &a, int r, T *red, Local<T> &L) {
         const bool is_push = have && (raw & (int)P1_FLAG);
         const bool is_pull = have && !(raw & (int)P1_FLAG);
         const int v = g - vw.delta;
+        // both rows of the entry up front: they do not depend on credits, so
+        // these loads need not wait for the unmark below, and the push after
+        // a lift finds its row already loaded
+        int pbeg = 0, pwork = 0, rbeg = 0, rwork = 0;
+        if (is_pull) {
+            pbeg = __ldg(a.A.row_ptr + v);
+            pwork = __ldg(a.A.row_ptr + v + 1) - pbeg;
+        }
+        if (have) {
+            rbeg = __ldg(a.A.rrow_ptr + v);
+            rwork = __ldg(a.A.rrow_ptr + v + 1) - rbeg;
+        }
         if (!L.on) {  // budget spent: the entries (still marked) join the next round's lists
-            const int work = !have ? 0
-                             : is_pull ? __ldg(a.A.row_ptr + v + 1) - __ldg(a.A.row_ptr + v)
-                                       : __ldg(a.A.rrow_ptr + v + 1) - __ldg(a.A.rrow_ptr + v);
+            const int work = is_pull ? pwork : rwork;
             stage_append(L.next_pull, is_pull, (unsigned)g, work);
             stage_append(L.next_push, is_push, (unsigned)g, work);
             continue;
@@ -690,11 +706,6 @@ __device__ void drain_local(const Args<T> &a, int r, T *red, Local<T> &L) {
             atom_and_acquire(bits + (g >> 5), ~(1u << (g & 31)));
         }
         // lifts
-        int pbeg = 0, pwork = 0;
-        if (is_pull) {
-            pbeg = __ldg(a.A.row_ptr + v);
-            pwork = __ldg(a.A.row_ptr + v + 1) - pbeg;
-        }
         int po;
         const int ptotal = warp_exclusive(pwork, po);
         T gmin = Cred<T>::TOP;
@@ -712,8 +723,8 @@ __device__ void drain_local(const Args<T> &a, int r, T *red, Local<T> &L) {
         // pushes: small ones here, large ones to the next round
         int qbeg = 0, qwork = 0;
         if (rose) {
-            qbeg = __ldg(a.A.rrow_ptr + v);
-            qwork = __ldg(a.A.rrow_ptr + v + 1) - qbeg;
+            qbeg = rbeg;
+            qwork = rwork;
         }
         const bool big = rose && qwork > a.local_maxdeg;
         {
@@ -1174,9 +1185,10 @@ __global__ void k_widen(const int *in, long long *out, int n) {
 // bound on finite credits), so the capped result is exact.
 //
 // A larger K proves more (a cycle of length L and weight -s needs K >= L/s),
-// but a player-0 cycle of weight 0 climbs only L per trip in the dual, so
-// the dual's cap costs about cap/L trips: the trials start at K = 8 and a
-// small B and grow both.
+// but the dual credits grow with K and so do the climbs that reach them:
+// the trials start at a small K (EG_OPT_DUAL_K, 4) and a small B and grow
+// both; from the second trial on the proven losses are frozen in the dual,
+// so its lift touches only the vertices still undecided.
 
 // OR of the finite credits into a bitmap (one warp per bitmap word).  With
 // an instance table that has an `active` array (batched solves), only the
@@ -1371,8 +1383,8 @@ static eg_status run_phase(eg_arena *ar, const SolveMem &m, StateBuffers &sb, co
 
 constexpr int CERT_TRIALS = 6;
 
-// Trials k = 0..5 with B = cap_certify * max|w'| * 4^k and K = 8^(k+1) (at
-// most n + 1).  A trial first lifts the game with cap B from the proven
+// Trials k = 0..5 with B = cap_certify * max|w'| * 4^k and K = dual_k * 8^k
+// (at most n + 1).  A trial first lifts the game with cap B from the proven
 // player-1 vertices at TOP; its finite vertices are proven player-0 wins.
 // If every vertex is then finite or proven lost, that capped fixpoint is
 // the least one.  Otherwise the dual is lifted with the proven player-0
@@ -1417,7 +1429,7 @@ static eg_status certify(eg_arena *ar, SolveMem &m, long long scale, long long s
         nproven = (long long)h[1];
         return EG_OK;
     };
-    long long K = std::min(8LL, n + 1);
+    long long K = std::min((long long)ar->dual_k, n + 1);
     for (int k = 0; k < CERT_TRIALS && B < C; ++k) {
         if (K > LIM / inner || B > LIM / (K + 1)) break;
         t.trials = k + 1;
@@ -1948,7 +1960,7 @@ static eg_status plan_certify(eg_plan_impl *p, cudaStream_t s, long long max_rou
             continue;
         }
         B[i] = mult * wm;
-        K[i] = std::min(8LL, (long long)p->n_of[i] + 1);
+        K[i] = std::min((long long)ar->dual_k, (long long)p->n_of[i] + 1);
         if (B[i] >= p->C[i]) direct[i] = 1;  // cap C: the capped lift is the exact one
         else if (!fits(i)) skip[i] = 1;
     }
