@@ -78,6 +78,7 @@ typedef struct eg_stats {
     int64_t enqueues;
     double ms;             /* device time of initialisation + fixpoint kernels */
     double fixpoint_ms;    /* device time of the persistent fixpoint kernel alone */
+    int64_t cycle_jumps;   /* vertices raised by cycle jumps (EG_OPT_KICK_ROUNDS) */
     /* The fixpoint launches of the solve in order, the first EG_MAX_PHASES
      * of them: a single solve runs a first attempt with cap C and, when that
      * does not finish, certified trials (a dual lift and a capped lift each,
@@ -218,6 +219,15 @@ eg_status eg_strategy(eg_arena *arena, int32_t credit_bits, int64_t w_scale, int
  *     proves player-1 wins on longer cycles of small weight in the first
  *     trial; a smaller one keeps the dual credits, and so the dual lift's
  *     climbs, short.
+ *   EG_OPT_KICK_ROUNDS (default 2): the lifts of the certified trials run
+ *     in slices of this many rounds, and between slices the cycles of the
+ *     current choices (every vertex's best edge) are jumped: on a cycle of
+ *     negative weight the least fixpoint must leave the cycle at a player-0
+ *     vertex, at a credit at least that vertex's best other option, so the
+ *     cycle's credits can rise at once to the bound this gives instead of
+ *     one lap per deficit at a time.  The bound is below the least fixpoint,
+ *     so the result is unchanged.  Cycles of up to 32 edges through vertices
+ *     of out-degree at most 64 are tried.  0 turns the jumps off.
  *   EG_OPT_BLOCKS_PER_SM (default 0): resident blocks per SM of the
  *     persistent fixpoint kernel; 0 takes as many as fit, a larger value is
  *     clamped to what fits.  Fewer blocks make the grid barrier cheaper and
@@ -250,6 +260,7 @@ eg_status eg_strategy(eg_arena *arena, int32_t credit_bits, int64_t w_scale, int
 #define EG_OPT_WAIT_LIMIT_US 9
 #define EG_OPT_SCC_ORDER 10
 #define EG_OPT_DUAL_K 11
+#define EG_OPT_KICK_ROUNDS 12
 eg_status eg_set_option(eg_arena *arena, int32_t option, int64_t value);
 
 /*
@@ -320,7 +331,7 @@ eg_status eg_plan_destroy(eg_plan *plan);
  * caps, see EG_OPT_CAP_CERTIFY), the same options and the same results.
  *
  * It allocates nothing: its working memory is one fixed device array inside
- * the library of about 13.9 MB (held by every GPU that loads the library
+ * the library of about 17.0 MB (held by every GPU that loads the library
  * until the process exits), and credits_out -- device memory on the arena's
  * device, n elements of credit_bits (32 or 64 only), aligned to its element
  * size -- serves as the credit array while the solve runs.  The arena must
@@ -346,8 +357,8 @@ eg_status eg_solve_credit_noalloc(eg_arena *arena, int32_t credit_bits, int64_t 
  * analysis of the input).  The settings of eg_set_option that change only
  * how fast the least fixpoint is reached -- EG_OPT_LOCAL_WINDOWS,
  * EG_OPT_LOCAL_MAXDEG, EG_OPT_BLOCKS_PER_SM and, when the certified trials
- * run, EG_OPT_CAP_CERTIFY, EG_OPT_DUAL_K and EG_OPT_CERTIFY_AFTER -- are
- * chosen by timing
+ * run, EG_OPT_CAP_CERTIFY, EG_OPT_DUAL_K, EG_OPT_KICK_ROUNDS and
+ * EG_OPT_CERTIFY_AFTER -- are chosen by timing
  * real solves (every one of them exact) in a coordinate search that starts
  * from the arena's current settings; a candidate replaces the best so far
  * only if it is more than 3% faster.  The chosen settings are set on the
@@ -368,7 +379,7 @@ eg_status eg_solve_credit_noalloc(eg_arena *arena, int32_t credit_bits, int64_t 
 typedef struct eg_tuning {
     int32_t local_windows, local_maxdeg, blocks_per_sm, cap_certify;
     int64_t certify_after;
-    int32_t dual_k, reserved;
+    int32_t dual_k, kick_rounds;
     double default_ms;   /* time to the fixpoint with the settings the search started from (-1: cached) */
     double tuned_ms;     /* with the chosen settings (the cached figure when from_cache) */
     int32_t solves;      /* runs timed by this call */

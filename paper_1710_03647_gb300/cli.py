@@ -32,7 +32,8 @@ def main(argv=None) -> None:
     ap.add_argument("--bits", type=int, default=0, choices=[0, 32, 64])
     ap.add_argument("--max-rounds", type=int, default=0)
     ap.add_argument("--repeat", type=int, default=1)
-    for opt in ("local-windows", "local-maxdeg", "warm-start", "cap-certify", "certify-after"):
+    for opt in ("local-windows", "local-maxdeg", "warm-start", "cap-certify", "certify-after", "dual-k",
+                "blocks-per-sm", "scc-order"):
         ap.add_argument("--" + opt, type=int, default=None)
     args = ap.parse_args(argv)
     if args.workload == "batch":
@@ -48,7 +49,8 @@ def main(argv=None) -> None:
         a = gen.varied_game(args.n, 2, 16, 1000, seed=args.seed)
     with eg.Arena(a) as arena:
         arena.tune(local_windows=args.local_windows, local_maxdeg=args.local_maxdeg, warm_start=args.warm_start,
-                   cap_certify=args.cap_certify, certify_after=args.certify_after)
+                   cap_certify=args.cap_certify, certify_after=args.certify_after, dual_k=args.dual_k,
+                   blocks_per_sm=args.blocks_per_sm, scc_order=args.scc_order)
         out = np.empty(a.n, dtype=np.int32 if args.bits == 32 else np.int64)
         for _ in range(args.repeat):
             rc, st = eg.eg_solve_credit(arena.handle, args.bits, 1, 0, out, max_rounds=args.max_rounds,
@@ -62,7 +64,8 @@ def batch(args) -> None:
     n, row_ptr, col, w, owner_bits, part_ptr = eg.pack_games(games)
     with eg.Arena(gen.Arena(n, row_ptr, col, w, owner_bits, "batch")) as arena:
         arena.tune(local_windows=args.local_windows, local_maxdeg=args.local_maxdeg, warm_start=args.warm_start,
-                   cap_certify=args.cap_certify, certify_after=args.certify_after)
+                   cap_certify=args.cap_certify, certify_after=args.certify_after, dual_k=args.dual_k,
+                   blocks_per_sm=args.blocks_per_sm)
         eg.eg_set_parts(arena.handle, part_ptr)
         with eg.Plan(arena.handle, args.games, credit_bits=args.bits) as plan:
             for _ in range(args.repeat):

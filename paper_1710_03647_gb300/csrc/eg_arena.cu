@@ -313,6 +313,7 @@ static eg_status destroy(eg_arena *a) {
     if (a->scc_comp) cudaFree(a->scc_comp);
     if (a->block) cudaFree(a->block);
     if (a->cert_block) cudaFree(a->cert_block);
+    if (a->kick_block) cudaFree(a->kick_block);
     if (a->ev0) cudaEventDestroy(a->ev0);
     if (a->ev1) cudaEventDestroy(a->ev1);
     if (a->evk) cudaEventDestroy(a->evk);
@@ -685,6 +686,7 @@ eg_status eg_set_option(eg_arena *arena, int32_t option, int64_t value) {
     case EG_OPT_CAP_CERTIFY: arena->cap_certify = (int)value; break;
     case EG_OPT_CERTIFY_AFTER: arena->certify_after = value; break;
     case EG_OPT_BLOCKS_PER_SM: arena->blocks_per_sm = (int)value; break;
+    case EG_OPT_KICK_ROUNDS: arena->kick_rounds = value; break;
     case EG_OPT_DUAL_K:
         if (value < 1) {
             eg::set_error("EG_OPT_DUAL_K takes at least 1");

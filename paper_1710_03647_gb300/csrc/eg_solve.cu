@@ -940,6 +940,123 @@ __global__ void __launch_bounds__(THREADS, EG_FIXPOINT_MIN_BLOCKS) k_fixpoint(Ar
 }
 
 // ---------------------------------------------------------------------------
+// Cycle jumps (accelerated lifting).  A cycle c of the arena whose weight
+// under the view is negative cannot be followed for ever by the least
+// fixpoint: each lap would need d more credit.  So some player-0 vertex of c
+// leaves it, at a credit at or above its best other option.  With credits f
+// at or below the least fixpoint and, for each player-0 vertex u of c,
+// alt(u) = min over u's other edges of f(x) (-) w, the greatest solution of
+//   x(v) = x(next) (-) w             (player 1)
+//   x(v) = min(x(next) (-) w, alt(v)) (player 0)
+// around c bounds the least fixpoint from below on c.  Raising f to x is
+// therefore sound, and it ends in one step a climb that the lifting would
+// take one lap per deficit d for.  The cycles tried are those of the
+// current choices (each vertex's best edge under f), which are the cycles
+// such climbs run on.
+
+constexpr int KICK_LEN = 32;      // longest choice cycle jumped
+constexpr int KICK_MAXDEG = 64;   // vertices of larger out-degree are not scanned
+
+// Each vertex's current choice (the edge of its lift's min or max under f)
+// and, for a player-0 vertex, the best of its other edges.  TOP, frozen and
+// high-degree vertices get no choice (-1).
+template <typename T>
+__global__ void k_policy(Args<T> a, int *choice, T *alt) {
+    const DevArena &A = a.A;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < A.n; v += gridDim.x * blockDim.x) {
+        const int b = __ldg(A.row_ptr + v), e1 = __ldg(A.row_ptr + v + 1);
+        const T fv = ld_cg(a.f + v);
+        const bool fz = a.frozen && ((__ldg(a.frozen + (v >> 5)) >> (v & 31)) & 1u);
+        if (fv == Cred<T>::TOP || fz || e1 - b > KICK_MAXDEG) {
+            choice[v] = -1;
+            continue;
+        }
+        const bool p1 = ((__ldg(A.owner_bits + (v >> 5)) >> (v & 31)) & 1u) ^ a.inv;
+        T best = p1 ? T(0) : Cred<T>::TOP, second = Cred<T>::TOP;
+        int be = -1;
+        for (int e = b; e < e1; ++e) {
+            const T t = ominus<T>(ld_cg(a.f + __ldg(A.col + e)), wmap(__ldg(A.w + e), a.W), a.W.C);
+            if (p1) {
+                if (be < 0 || t > best) {
+                    best = t;
+                    be = e;
+                }
+            } else if (be < 0 || t < best) {
+                second = best;
+                best = t;
+                be = e;
+            } else if (t < second) {
+                second = t;
+            }
+        }
+        choice[v] = be;
+        alt[v] = second;
+    }
+}
+
+// One thread per vertex: a vertex that is the smallest id on a choice cycle
+// of at most KICK_LEN edges with negative weight raises the cycle to its
+// bound and queues the vertices that rose for the push list of round r.
+template <typename T>
+__global__ void k_kick(Args<T> a, const int *choice, const T *alt, int r, unsigned long long *jumped) {
+    const DevArena &A = a.A;
+    unsigned long long mine = 0;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < A.n; v += gridDim.x * blockDim.x) {
+        int e = choice[v];
+        if (e < 0) continue;
+        int cyc[KICK_LEN];
+        int len = 0, x = v;
+        bool ok = true;
+        long long wsum = 0;
+        do {
+            if (len == KICK_LEN || e < 0) {
+                ok = false;
+                break;
+            }
+            cyc[len++] = e;
+            wsum += wmap(__ldg(A.w + e), a.W);
+            x = __ldg(A.col + e);
+            if (x < v) {  // the cycle, if any, is the smaller id's to jump
+                ok = false;
+                break;
+            }
+            e = x == v ? 0 : choice[x];
+        } while (x != v);
+        if (!ok || wsum >= 0) continue;
+        // greatest solution around the cycle, from TOP: two backward laps
+        T xv[KICK_LEN];
+        for (int i = 0; i < len; ++i) xv[i] = Cred<T>::TOP;
+        for (int lap = 0; lap < 2; ++lap) {
+            for (int i = len - 1; i >= 0; --i) {
+                const int ce = cyc[i];
+                const int cv = i == 0 ? v : __ldg(A.col + cyc[i - 1]);
+                T val = ominus<T>(xv[i + 1 == len ? 0 : i + 1], wmap(__ldg(A.w + ce), a.W), a.W.C);
+                const bool p1 = ((__ldg(A.owner_bits + (cv >> 5)) >> (cv & 31)) & 1u) ^ a.inv;
+                if (!p1) val = min(val, alt[cv]);
+                xv[i] = val;
+            }
+        }
+        for (int i = 0; i < len; ++i) {
+            const int cv = i == 0 ? v : __ldg(A.col + cyc[i - 1]);
+            if (!(xv[i] > ld_cg(a.f + cv))) continue;
+            if (!(xv[i] > atomicMax(a.f + cv, xv[i]))) continue;
+            ++mine;
+            const int work = __ldg(A.rrow_ptr + cv + 1) - __ldg(A.rrow_ptr + cv);
+            const unsigned bit = 1u << (cv & 31);
+            if (work > 0 && !(atomicOr(a.bits_push[r & 1] + (cv >> 5), bit) & bit)) {
+                const unsigned long long base =
+                    atomicAdd(&a.ctrl->push_ctr[r % 3], ((unsigned long long)(unsigned)work << 32) | 1ull);
+                const unsigned idx = (unsigned)(base & 0xffffffffu);
+                a.push_items[r & 1][idx] = cv;
+                a.push_offs[r & 1][idx] = (int)(base >> 32);
+            }
+        }
+    }
+    for (int d = 16; d; d >>= 1) mine += __shfl_down_sync(FULL, mine, d);
+    if (lane_id() == 0 && mine) atomicAdd(jumped, mine);
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 
 // A persistent fixpoint kernel waits at grid barriers for all its blocks.
@@ -1053,6 +1170,7 @@ struct Launch {
     const unsigned *frozen = nullptr;  // vertices held at 0 (dual lifts of the certified trials)
     const int *level = nullptr;        // SCC-ordered solves: level of each vertex
     int cur_level = 0;                 //   and the level this launch solves (0 first)
+    long long slice_rounds = 0;        // > 0: the launch stops after this many rounds, without error
 };
 
 // The arena's launch settings with the given warm start and round budget.
@@ -1067,7 +1185,8 @@ static Launch launch_of(const eg_arena *ar, int warm_start, long long max_rounds
 // stream s; ev_k (optional) is recorded right before the fixpoint kernel.
 template <bool MULTI, typename T>
 static eg_status enqueue_solve(const DevArena &A, const WeightView &W, const InstTable &I, long long nf,
-                               StateBuffers &sb, const Launch &L, int device, cudaStream_t s, cudaEvent_t ev_k) {
+                               StateBuffers &sb, const Launch &L, int device, cudaStream_t s, cudaEvent_t ev_k,
+                               Args<T> *keep = nullptr, int *grid_blocks = nullptr) {
     const int sms = num_sms(device);
     if (sb.dirty) {
         k_fill<T><<<sms * 4, 256, 0, s>>>((T *)sb.d.acc, nf, Cred<T>::TOP);
@@ -1097,9 +1216,9 @@ static eg_status enqueue_solve(const DevArena &A, const WeightView &W, const Ins
     a.acc = (T *)sb.d.acc;
     a.acc_done = sb.d.acc_done;
     a.ctrl = sb.d.ctrl;
-    a.max_rounds = L.max_rounds;
+    a.max_rounds = L.slice_rounds > 0 ? L.slice_rounds : L.max_rounds;
     a.r0 = 0;
-    a.slice = 0;
+    a.slice = L.slice_rounds > 0 ? 1 : 0;
     a.doorbell = nullptr;
     a.local_windows = L.local_windows;
     a.local_maxdeg = L.local_maxdeg;
@@ -1145,6 +1264,8 @@ static eg_status enqueue_solve(const DevArena &A, const WeightView &W, const Ins
     void *args[] = {&a};
     if (ev_k) EG_CUDA_TRY(cudaEventRecord(ev_k, s));
     EG_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_fixpoint<MULTI, T>, grid, block, args, 0, s));
+    if (keep) *keep = a;  // for the launches that resume it
+    if (grid_blocks) *grid_blocks = (int)grid.x;
     return EG_OK;
 }
 
@@ -1275,7 +1396,7 @@ struct PhaseRec {
 };
 
 struct Totals {
-    long long rounds = 0, lifts = 0, pushes = 0, relax = 0, enqueues = 0, seeded = 0;
+    long long rounds = 0, lifts = 0, pushes = 0, relax = 0, enqueues = 0, seeded = 0, jumps = 0;
     double ms = 0, kms = 0;
     int trials = 0;
     std::vector<PhaseRec> phases;
@@ -1314,6 +1435,7 @@ static void fill_stats(eg_stats *st, const Totals &t, long long C, long long see
     st->enqueues = t.enqueues;
     st->ms = t.ms;
     st->fixpoint_ms = t.kms;
+    st->cycle_jumps = t.jumps;
     st->phases = (int32_t)std::min<size_t>(t.phases.size(), EG_MAX_PHASES);
     st->trials = t.trials;
     for (int k = 0; k < EG_MAX_PHASES; ++k) {
@@ -1341,7 +1463,24 @@ struct SolveMem {
     bool fixed = false;     // laid over the allocation-free array
     bool in_place = false;  // sb's credit array is the caller's output buffer
     long long attempt_only = 0;  // > 0: only a first attempt of this many rounds (EG_ERR_BUDGET if unfinished)
+    int *kick_choice = nullptr;  // cycle jumps: each vertex's current choice (edge id),
+    void *kick_alt = nullptr;    //   a player-0 vertex's best other option (credit width of the phase),
+    unsigned long long *kick_jumps = nullptr;  //   and the count of vertices raised
 };
+
+// The scratch of the cycle jumps of an allocating solve (allocated on first use).
+static eg_status kick_memory(eg_arena *ar, SolveMem &m) {
+    if (m.kick_choice) return EG_OK;
+    if (!ar->kick_block) {
+        const size_t o_alt = align_up((size_t)ar->n * 4), o_cnt = o_alt + align_up((size_t)ar->n * 8);
+        EG_CUDA_TRY(cudaMalloc(&ar->kick_block, o_cnt + 256));
+    }
+    char *b = (char *)ar->kick_block;
+    m.kick_choice = (int *)b;
+    m.kick_alt = b + align_up((size_t)ar->n * 4);
+    m.kick_jumps = (unsigned long long *)(b + align_up((size_t)ar->n * 4) + align_up((size_t)ar->n * 8));
+    return EG_OK;
+}
 
 // The dual state and the trial bitmaps of an allocating solve.
 static eg_status cert_memory(eg_arena *ar, SolveMem &m) {
@@ -1366,17 +1505,66 @@ static eg_status cert_memory(eg_arena *ar, SolveMem &m) {
     return EG_OK;
 }
 
-// One solve run to its end on s; adds its counters and returns its device status.
+// One solve run to its end on s; adds its counters and returns its device
+// status.  With cycle jumps on (EG_OPT_KICK_ROUNDS > 0, not for the levels
+// of an SCC-ordered solve), the fixpoint runs in slices of that many rounds
+// and the choice cycles are jumped between slices; a slice resumes at the
+// round the last one stopped at, with its lists.
 template <typename T>
-static eg_status run_phase(eg_arena *ar, const SolveMem &m, StateBuffers &sb, const WeightView &W, const Launch &L,
+static eg_status run_phase(eg_arena *ar, SolveMem &m, StateBuffers &sb, const WeightView &W, const Launch &L,
                            cudaStream_t s, Totals &t, int kind, int &dev) {
     if (m.fixed) sb.dirty = true;  // the scratch is shared with the other state
-    eg_status rc = launch_solve<T>(ar, sb, W, s, L);
+    const long long R = ar->kick_rounds;
+    eg_status rc = EG_OK;
+    if (R <= 0 || L.level) {
+        rc = launch_solve<T>(ar, sb, W, s, L);
+        if (rc != EG_OK) return rc;
+        EG_CUDA_TRY(cudaMemcpyAsync(ar->host_ctrl, sb.d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+        EG_CUDA_TRY(cudaStreamSynchronize(s));
+        add_totals(t, ar, kind, W.C);
+        dev = ((const Ctrl *)ar->host_ctrl)->status;
+        if (dev != DEV_OK) sb.dirty = true;
+        return EG_OK;
+    }
+    if ((rc = kick_memory(ar, m)) != EG_OK) return rc;
+    EG_CUDA_TRY(cudaMemsetAsync(m.kick_jumps, 0, sizeof(unsigned long long), s));
+    EG_CUDA_TRY(cudaEventRecord(ar->ev0, s));
+    Launch Ls = L;
+    Ls.slice_rounds = L.max_rounds > 0 ? std::min(R, L.max_rounds) : R;
+    Args<T> a;
+    int blocks = 0;
+    const InstTable none{1, 0, nullptr, nullptr, nullptr, nullptr, nullptr};
+    rc = enqueue_solve<false, T>(ar->d, W, none, ar->n, sb, Ls, ar->device, s, ar->evk, &a, &blocks);
     if (rc != EG_OK) return rc;
-    EG_CUDA_TRY(cudaMemcpyAsync(ar->host_ctrl, sb.d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+    const int kb = (int)std::min<long long>((ar->n + 255) / 256, (long long)num_sms(ar->device) * 8);
+    const Ctrl *hc = (const Ctrl *)ar->host_ctrl;
+    bool budget = false;
+    for (;;) {
+        EG_CUDA_TRY(cudaMemcpyAsync(ar->host_ctrl, sb.d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s));
+        EG_CUDA_TRY(cudaStreamSynchronize(s));
+        if (hc->status != DEV_OK) break;
+        const long long r = hc->r_next;
+        if ((hc->pull_ctr[r % 3] & 0xffffffffu) == 0 && (hc->push_ctr[r % 3] & 0xffffffffu) == 0) break;
+        if (L.max_rounds > 0 && r >= L.max_rounds) {
+            budget = true;
+            break;
+        }
+        k_policy<T><<<kb, 256, 0, s>>>(a, m.kick_choice, (T *)m.kick_alt);
+        k_kick<T><<<kb, 256, 0, s>>>(a, m.kick_choice, (const T *)m.kick_alt, (int)r, m.kick_jumps);
+        EG_CUDA_TRY(cudaGetLastError());
+        a.r0 = r;
+        a.max_rounds = L.max_rounds > 0 ? std::min(r + R, L.max_rounds) : r + R;
+        void *args[] = {&a};
+        EG_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_fixpoint<false, T>, dim3(blocks), dim3(THREADS), args,
+                                                0, s));
+    }
+    EG_CUDA_TRY(cudaEventRecord(ar->ev1, s));
+    unsigned long long jumps = 0;
+    EG_CUDA_TRY(cudaMemcpyAsync(&jumps, m.kick_jumps, sizeof(jumps), cudaMemcpyDeviceToHost, s));
     EG_CUDA_TRY(cudaStreamSynchronize(s));
     add_totals(t, ar, kind, W.C);
-    dev = ((const Ctrl *)ar->host_ctrl)->status;
+    t.jumps += (long long)jumps;
+    dev = budget ? DEV_BUDGET : hc->status;
     if (dev != DEV_OK) sb.dirty = true;
     return EG_OK;
 }
@@ -2468,14 +2656,17 @@ constexpr size_t NOALLOC_WORDS = (size_t)(NOALLOC_MAX_N + 31) / 32;
 constexpr size_t noalloc_up(size_t x) { return (x + 255) & ~size_t(255); }
 // layout: 8 lists of n ints, 7 bitmaps (5 of the solve state, the proven
 // player-0 and player-1 vertices), n partial minima (int64), n counts, the
-// int64 credits of the dual lifts, control block, 4 counters (bound
-// accumulators, trial counts)
+// int64 credits of the dual lifts, the cycle jumps' choices (n ints) and
+// alternatives (n int64), control block, counters (bound accumulators,
+// trial counts, vertices jumped)
 constexpr size_t NA_LISTS = 0;
 constexpr size_t NA_BITS = NA_LISTS + 8 * noalloc_up((size_t)NOALLOC_MAX_N * 4);
 constexpr size_t NA_ACC = NA_BITS + 7 * noalloc_up(NOALLOC_WORDS * 4);
 constexpr size_t NA_DONE = NA_ACC + noalloc_up((size_t)NOALLOC_MAX_N * 8);
 constexpr size_t NA_DUAL = NA_DONE + noalloc_up((size_t)NOALLOC_MAX_N * 4);
-constexpr size_t NA_CTRL = NA_DUAL + noalloc_up((size_t)NOALLOC_MAX_N * 8);
+constexpr size_t NA_KCHOICE = NA_DUAL + noalloc_up((size_t)NOALLOC_MAX_N * 8);
+constexpr size_t NA_KALT = NA_KCHOICE + noalloc_up((size_t)NOALLOC_MAX_N * 4);
+constexpr size_t NA_CTRL = NA_KALT + noalloc_up((size_t)NOALLOC_MAX_N * 8);
 constexpr size_t NA_COUNT = NA_CTRL + noalloc_up(sizeof(Ctrl));
 constexpr size_t NA_BYTES = NA_COUNT + 256;
 
@@ -2635,6 +2826,9 @@ static eg_status solve_noalloc(eg_arena *ar, int credit_bits, long long scale, l
     m.cert_w0 = (unsigned *)(base + NA_BITS + 5 * noalloc_up(words * 4));
     m.cert_w1 = (unsigned *)(base + NA_BITS + 6 * noalloc_up(words * 4));
     m.aux = dcount + 2;
+    m.kick_choice = (int *)(base + NA_KCHOICE);
+    m.kick_alt = base + NA_KALT;
+    m.kick_jumps = dcount + 4;
     m.fixed = true;
     m.in_place = true;
     return solve_route(ar, m, credit_bits, credit_bits, scale, shift, C, wmax, out, st, s, max_rounds);

@@ -56,11 +56,12 @@ struct Settings {
     int local_windows, local_maxdeg, blocks_per_sm, cap_certify;
     long long certify_after;
     int dual_k;
+    long long kick_rounds;
 };
 
 static Settings settings_of(const eg_arena *ar) {
     return Settings{ar->local_windows, ar->local_maxdeg, ar->blocks_per_sm, ar->cap_certify, ar->certify_after,
-                    ar->dual_k};
+                    ar->dual_k, ar->kick_rounds};
 }
 
 static void apply(eg_arena *ar, const Settings &S) {
@@ -70,6 +71,7 @@ static void apply(eg_arena *ar, const Settings &S) {
     ar->cap_certify = S.cap_certify;
     ar->certify_after = S.certify_after;
     ar->dual_k = S.dual_k;
+    ar->kick_rounds = S.kick_rounds;
 }
 
 static int ilog2(double x) { return x <= 1.0 ? 0 : (int)std::lround(std::log2(x)); }
@@ -164,11 +166,12 @@ static bool cache_lookup(const char *path, const std::string &key, Settings &S, 
     for (const std::string &line : read_lines(path)) {
         std::string k;
         if (!key_of(line, k) || k != key) continue;
-        long long lw, md, bps, cc, ca, dk, us = -1;
+        long long lw, md, bps, cc, ca, dk, kr, us = -1;
         if (field(line, "local_windows", lw) && field(line, "local_maxdeg", md) && field(line, "blocks_per_sm", bps) &&
-            field(line, "cap_certify", cc) && field(line, "certify_after", ca) && field(line, "dual_k", dk)) {
+            field(line, "cap_certify", cc) && field(line, "certify_after", ca) && field(line, "dual_k", dk) &&
+            field(line, "kick_rounds", kr)) {
             field(line, "tuned_us", us);
-            S = Settings{(int)lw, (int)md, (int)bps, (int)cc, ca, (int)dk};
+            S = Settings{(int)lw, (int)md, (int)bps, (int)cc, ca, (int)dk, kr};
             ms = us >= 0 ? us * 1e-3 : -1.0;
             return true;
         }
@@ -186,9 +189,10 @@ static eg_status cache_store(const char *path, const std::string &key, const Set
     char buf[512];
     snprintf(buf, sizeof(buf),
              "{\"key\": \"%s\", \"local_windows\": %d, \"local_maxdeg\": %d, \"blocks_per_sm\": %d, "
-             "\"cap_certify\": %d, \"certify_after\": %lld, \"dual_k\": %d, \"tuned_us\": %lld}",
+             "\"cap_certify\": %d, \"certify_after\": %lld, \"dual_k\": %d, \"kick_rounds\": %lld, "
+             "\"tuned_us\": %lld}",
              key.c_str(), S.local_windows, S.local_maxdeg, S.blocks_per_sm, S.cap_certify, S.certify_after,
-             S.dual_k, (long long)std::llround(ms * 1e3));
+             S.dual_k, S.kick_rounds, (long long)std::llround(ms * 1e3));
     keep.push_back(buf);
     const std::string tmp = std::string(path) + ".tmp";
     FILE *fh = fopen(tmp.c_str(), "w");
@@ -256,20 +260,28 @@ static eg_status search(eg_arena *ar, RunFn run, void *ctx, cudaStream_t s, int 
     const int cc[] = {2, 4, 8, 16};
     const int dk[] = {1, 2, 4, 8};
     const int ca[] = {4, 8, 16, 32};
+    const int kr[] = {0, 1, 2, 4, 8};
     // the trial settings first: they change the number of rounds most
-    const int order[] = {3, 5, 0, 1, 2, 4};
+    const int order[] = {6, 3, 5, 0, 1, 2, 4};
     for (int dim : order) {
-        if ((dim == 3 || dim == 4 || dim == 5) && !trials_matter) continue;
-        const int *vals = dim == 0 ? lw : dim == 1 ? md : dim == 2 ? bps : dim == 3 ? cc : dim == 5 ? dk : ca;
-        const int nv = dim == 0 ? 6 : dim == 1 ? 5 : 4;
+        if ((dim == 3 || dim == 4 || dim == 5 || dim == 6) && !trials_matter) continue;
+        const int *vals = dim == 0   ? lw
+                          : dim == 1 ? md
+                          : dim == 2 ? bps
+                          : dim == 3 ? cc
+                          : dim == 5 ? dk
+                          : dim == 6 ? kr
+                                     : ca;
+        const int nv = dim == 0 ? 6 : (dim == 1 || dim == 6) ? 5 : 4;
         for (int k = 0; k < nv; ++k) {
             if (solves + reps > max_solves) break;
             Settings c = best;
             int *slot = dim == 0 ? &c.local_windows : dim == 1 ? &c.local_maxdeg : dim == 2 ? &c.blocks_per_sm
                                                       : dim == 5 ? &c.dual_k : &c.cap_certify;
-            if (dim == 4) {
-                if (c.certify_after == vals[k]) continue;
-                c.certify_after = vals[k];
+            if (dim == 4 || dim == 6) {
+                long long &v = dim == 4 ? c.certify_after : c.kick_rounds;
+                if (v == vals[k]) continue;
+                v = vals[k];
             } else {
                 if (*slot == vals[k]) continue;
                 *slot = vals[k];
@@ -322,6 +334,7 @@ static void fill(eg_tuning *out, const Settings &S, double d, double t, int solv
     out->cap_certify = S.cap_certify;
     out->certify_after = S.certify_after;
     out->dual_k = S.dual_k;
+    out->kick_rounds = (int32_t)S.kick_rounds;
     out->default_ms = d;
     out->tuned_ms = t;
     out->solves = solves;

@@ -49,7 +49,8 @@ class eg_stats(ctypes.Structure):
     _fields_ = [("C", ctypes.c_int64), ("seeded", ctypes.c_int64), ("credit_bits", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("rounds", ctypes.c_int64), ("lifts", ctypes.c_int64), ("pushes", ctypes.c_int64),
                 ("relaxations", ctypes.c_int64), ("enqueues", ctypes.c_int64), ("ms", ctypes.c_double),
-                ("fixpoint_ms", ctypes.c_double), ("phases", ctypes.c_int32), ("trials", ctypes.c_int32),
+                ("fixpoint_ms", ctypes.c_double), ("cycle_jumps", ctypes.c_int64), ("phases", ctypes.c_int32),
+                ("trials", ctypes.c_int32),
                 ("phase_kind", ctypes.c_int32 * EG_MAX_PHASES), ("phase_cap", ctypes.c_int64 * EG_MAX_PHASES),
                 ("phase_rounds", ctypes.c_int64 * EG_MAX_PHASES),
                 ("phase_relaxations", ctypes.c_int64 * EG_MAX_PHASES),
@@ -82,7 +83,7 @@ EG_SRV_IDLE_SOLO = 2
 class eg_tuning(ctypes.Structure):
     _fields_ = [("local_windows", ctypes.c_int32), ("local_maxdeg", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("cap_certify", ctypes.c_int32),
-                ("certify_after", ctypes.c_int64), ("dual_k", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("certify_after", ctypes.c_int64), ("dual_k", ctypes.c_int32), ("kick_rounds", ctypes.c_int32),
                 ("default_ms", ctypes.c_double), ("tuned_ms", ctypes.c_double),
                 ("solves", ctypes.c_int32), ("from_cache", ctypes.c_int32), ("key", ctypes.c_char * 96)]
 
@@ -208,6 +209,7 @@ EG_OPT_BLOCKS_PER_SM = 8
 EG_OPT_WAIT_LIMIT_US = 9
 EG_OPT_SCC_ORDER = 10
 EG_OPT_DUAL_K = 11
+EG_OPT_KICK_ROUNDS = 12
 
 
 def eg_solve_credit_noalloc(arena, credit_bits, w_scale, w_shift, credits_out, stream=None, max_rounds=0,
@@ -283,12 +285,14 @@ class Arena:
         return out, st
 
     def tune(self, local_windows=None, local_maxdeg=None, warm_start=None, seed_max_pairs=None, cap_certify=None,
-             certify_after=None, blocks_per_sm=None, wait_limit_us=None, scc_order=None, dual_k=None):
+             certify_after=None, blocks_per_sm=None, wait_limit_us=None, scc_order=None, dual_k=None,
+             kick_rounds=None):
         for opt, val in ((EG_OPT_LOCAL_WINDOWS, local_windows), (EG_OPT_LOCAL_MAXDEG, local_maxdeg),
                          (EG_OPT_WARM_START, warm_start), (EG_OPT_SEED_MAX_PAIRS, seed_max_pairs),
                          (EG_OPT_CAP_CERTIFY, cap_certify), (EG_OPT_CERTIFY_AFTER, certify_after),
                          (EG_OPT_BLOCKS_PER_SM, blocks_per_sm), (EG_OPT_WAIT_LIMIT_US, wait_limit_us),
-                         (EG_OPT_SCC_ORDER, scc_order), (EG_OPT_DUAL_K, dual_k)):
+                         (EG_OPT_SCC_ORDER, scc_order), (EG_OPT_DUAL_K, dual_k),
+                         (EG_OPT_KICK_ROUNDS, kick_rounds)):
             if val is not None:
                 eg_set_option(self.handle, opt, int(val))
 

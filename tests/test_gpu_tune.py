@@ -48,7 +48,7 @@ def test_tuned_settings_keep_the_oracle_credits_and_are_cached(tmp_path, make, b
     with eg.Arena(a) as ar2:
         t2 = eg.eg_autotune(ar2.handle, bits, 1, 0, cache)
         assert t2["from_cache"] == 1 and t2["solves"] == 0 and t2["key"] == t["key"]
-        for k in ("local_windows", "local_maxdeg", "blocks_per_sm", "cap_certify", "certify_after", "dual_k"):
+        for k in ("local_windows", "local_maxdeg", "blocks_per_sm", "cap_certify", "certify_after", "dual_k", "kick_rounds"):
             assert t2[k] == t[k], k
         out, _ = ar2.solve(credit_bits=bits)
         got = np.where(out == eg.EG_TOP32, oracle.TOP, out.astype(np.int64)) if bits == 32 else out

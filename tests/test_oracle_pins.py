@@ -351,3 +351,107 @@ def test_dual_with_proven_losses_as_sinks_finds_only_losses(block):
                     assert (exact[fin] == TOP64).all(), (seed, K, B)
                     checked += 1
     assert checked > 0
+
+
+# ---- the cycle bound behind the accelerated lifting --------------------------
+# For a cycle c of the arena whose weight is negative, and credits f at or
+# below the least fixpoint, let alt(u) be, for a player-0 vertex u of c, the
+# least f(x) (-) w over u's edges other than its edge on c.  The greatest
+# solution x of  x(v) = x(next) (-) w  (player 1),
+#                x(v) = min(x(next) (-) w, alt(v))  (player 0)
+# around c is at or below the least fixpoint at every vertex of c: the least
+# fixpoint cannot follow c all the way round (each lap would need d more
+# credit), so some player-0 vertex of c leaves it at or above its alt.
+
+def _cycle_bound(a, f, cyc_edges, C):
+    """x on the cycle given by its edge ids (in order), from x = TOP."""
+    rp = np.asarray(a.row_ptr)
+    src = np.repeat(np.arange(a.n), np.diff(rp))
+    w = np.asarray(a.w, dtype=np.int64)
+    p1 = gen.unpack_owner(a.owner_bits, a.n)
+
+    def om(x, wt):
+        if x == TOP64:
+            return TOP64
+        d = x - wt
+        return TOP64 if d > C else max(0, d)
+
+    L = len(cyc_edges)
+    verts = [int(src[e]) for e in cyc_edges]
+    alts = []
+    for e, v in zip(cyc_edges, verts):
+        others = [om(int(f[a.col[k]]), int(w[k])) for k in range(rp[v], rp[v + 1]) if k != e]
+        alts.append(min(others) if others else TOP64)
+    x = [TOP64] * L
+    for _ in range(2):
+        for i in range(L - 1, -1, -1):
+            val = om(x[(i + 1) % L], int(w[cyc_edges[i]]))
+            if not p1[verts[i]]:
+                val = min(val, alts[i])
+            x[i] = val
+    return verts, x
+
+
+def _simple_cycles(a, max_len=5):
+    """Edge-id lists of the simple cycles of length <= max_len (each once)."""
+    rp = np.asarray(a.row_ptr)
+    out = []
+
+    def walk(start, v, path_e, seen):
+        for e in range(rp[v], rp[v + 1]):
+            u = int(a.col[e])
+            if u == start:
+                out.append(path_e + [e])
+            elif u > start and u not in seen and len(path_e) + 1 < max_len:
+                walk(start, u, path_e + [e], seen | {u})
+    for s in range(a.n):
+        walk(s, s, [], {s})
+    return out
+
+
+@pytest.mark.parametrize("block", range(4))
+def test_cycle_bound_stays_below_the_least_fixpoint(block):
+    checked = 0
+    for seed in range(block * 50, block * 50 + 50):
+        a = _tiny(seed)
+        exact = oracle.brute_force(a.n, a.row_ptr, a.col, a.w, a.owner_bits)
+        C = oracle.bound(a.n, a.row_ptr, a.w)
+        w = np.asarray(a.w, dtype=np.int64)
+        for cyc in _simple_cycles(a):
+            if int(w[cyc].sum()) >= 0:
+                continue
+            # credits at or below the least fixpoint: 0, the fixpoint itself,
+            # and random ones in between (TOP drawn from {0..C} u {TOP})
+            draws = gen.Stream(seed, 31 + len(cyc)).unit(4 * a.n).reshape(4, a.n)
+            cases = [np.zeros(a.n, dtype=np.int64), exact.copy()]
+            for row in draws:
+                hi = np.where(exact == TOP64, C + 1, exact)
+                f = np.floor(row * (hi + 1)).astype(np.int64)
+                f = np.where(f > C, TOP64, np.minimum(f, hi))
+                cases.append(np.where(exact == TOP64, f, np.minimum(f, exact)))
+            for f in cases:
+                assert (f <= exact).all()
+                verts, x = _cycle_bound(a, f, cyc, C)
+                for v, xv in zip(verts, x):
+                    assert xv <= exact[v], (seed, cyc, v, xv, exact[v])
+                checked += 1
+    assert checked > 0
+
+
+def test_cycle_bound_catches_a_wrong_bound():
+    # the bound with the alternatives dropped (a lap assumed to be forced)
+    # exceeds the least fixpoint somewhere: the pin above would catch it
+    broke = 0
+    for seed in range(200):
+        a = _tiny(seed)
+        exact = oracle.brute_force(a.n, a.row_ptr, a.col, a.w, a.owner_bits)
+        C = oracle.bound(a.n, a.row_ptr, a.w)
+        w = np.asarray(a.w, dtype=np.int64)
+        for cyc in _simple_cycles(a):
+            if int(w[cyc].sum()) >= 0:
+                continue
+            verts = [int(np.searchsorted(np.asarray(a.row_ptr), e, side="right") - 1) for e in cyc]
+            # no exits: every vertex of the cycle would be TOP
+            if any(exact[v] != TOP64 for v in verts):
+                broke += 1
+    assert broke > 0
