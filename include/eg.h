@@ -331,7 +331,7 @@ eg_status eg_plan_destroy(eg_plan *plan);
  * caps, see EG_OPT_CAP_CERTIFY), the same options and the same results.
  *
  * It allocates nothing: its working memory is one fixed device array inside
- * the library of about 17.0 MB (held by every GPU that loads the library
+ * the library of about 14.9 MB (held by every GPU that loads the library
  * until the process exits), and credits_out -- device memory on the arena's
  * device, n elements of credit_bits (32 or 64 only), aligned to its element
  * size -- serves as the credit array while the solve runs.  The arena must

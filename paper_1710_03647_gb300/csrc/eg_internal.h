@@ -107,6 +107,7 @@ struct eg_arena {
     int dual_k = 4;                   // weight multiplier K of the first trial's dual lift
     long long kick_rounds = 2;        // rounds between cycle jumps of the trials' lifts (0: none)
     void *kick_block = nullptr;       // scratch of the cycle jumps (allocated on first use)
+    unsigned kick_epoch = 0;          // epoch counter of its claim array
     long long certify_after = 64;     // rounds of a first solve with cap C before the trial caps (0: none); eg_create sets the default
     int blocks_per_sm = 0;            // resident blocks per SM of the fixpoint kernel (0: as many as fit)
     int scc_order = 0;                // solve by the topological levels of the strongly connected components

@@ -955,91 +955,94 @@ __global__ void __launch_bounds__(THREADS, EG_FIXPOINT_MIN_BLOCKS) k_fixpoint(Ar
 // such climbs run on.
 
 constexpr int KICK_LEN = 32;      // longest choice cycle jumped
-constexpr int KICK_MAXDEG = 64;   // vertices of larger out-degree are not scanned
+constexpr int KICK_MAXDEG = 64;   // vertices of larger out-degree have no choice
 
-// Each vertex's current choice (the edge of its lift's min or max under f)
-// and, for a player-0 vertex, the best of its other edges.  TOP, frozen and
-// high-degree vertices get no choice (-1).
+// The current choice of vertex x (the edge of its lift's min or max under f)
+// and, for a player-0 vertex, the best of its other edges; false if x has
+// none (at TOP, frozen, or of out-degree above KICK_MAXDEG).
 template <typename T>
-__global__ void k_policy(Args<T> a, int *choice, T *alt) {
+__device__ __forceinline__ bool choice_of(const Args<T> &a, int x, int &edge, T &alt) {
     const DevArena &A = a.A;
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < A.n; v += gridDim.x * blockDim.x) {
-        const int b = __ldg(A.row_ptr + v), e1 = __ldg(A.row_ptr + v + 1);
-        const T fv = ld_cg(a.f + v);
-        const bool fz = a.frozen && ((__ldg(a.frozen + (v >> 5)) >> (v & 31)) & 1u);
-        if (fv == Cred<T>::TOP || fz || e1 - b > KICK_MAXDEG) {
-            choice[v] = -1;
-            continue;
-        }
-        const bool p1 = ((__ldg(A.owner_bits + (v >> 5)) >> (v & 31)) & 1u) ^ a.inv;
-        T best = p1 ? T(0) : Cred<T>::TOP, second = Cred<T>::TOP;
-        int be = -1;
-        for (int e = b; e < e1; ++e) {
-            const T t = ominus<T>(ld_cg(a.f + __ldg(A.col + e)), wmap(__ldg(A.w + e), a.W), a.W.C);
-            if (p1) {
-                if (be < 0 || t > best) {
-                    best = t;
-                    be = e;
-                }
-            } else if (be < 0 || t < best) {
-                second = best;
+    const int b = __ldg(A.row_ptr + x), e1 = __ldg(A.row_ptr + x + 1);
+    if (e1 - b > KICK_MAXDEG || ld_cg(a.f + x) == Cred<T>::TOP) return false;
+    if (a.frozen && ((__ldg(a.frozen + (x >> 5)) >> (x & 31)) & 1u)) return false;
+    const bool p1 = ((__ldg(A.owner_bits + (x >> 5)) >> (x & 31)) & 1u) ^ a.inv;
+    T best = p1 ? T(0) : Cred<T>::TOP, second = Cred<T>::TOP;
+    int be = -1;
+    for (int e = b; e < e1; ++e) {
+        const T t = ominus<T>(ld_cg(a.f + __ldg(A.col + e)), wmap(__ldg(A.w + e), a.W), a.W.C);
+        if (p1) {
+            if (be < 0 || t > best) {
                 best = t;
                 be = e;
-            } else if (t < second) {
-                second = t;
             }
+        } else if (be < 0 || t < best) {
+            second = best;
+            best = t;
+            be = e;
+        } else if (t < second) {
+            second = t;
         }
-        choice[v] = be;
-        alt[v] = second;
     }
+    edge = be;
+    alt = second;
+    return be >= 0;
 }
 
-// One thread per vertex: a vertex that is the smallest id on a choice cycle
-// of at most KICK_LEN edges with negative weight raises the cycle to its
-// bound and queues the vertices that rose for the push list of round r.
+// One thread per entry of round r's pull and push lists: the walk along the
+// current choices from the entry, computed as it goes; if it returns to the
+// entry within KICK_LEN edges and the cycle's weight is negative, the cycle
+// is claimed for this epoch at its smallest vertex (one jump per cycle),
+// raised to its bound, and the vertices that rose join round r's push list.
+// A climbing cycle always has a vertex in the lists, so scanning them finds
+// the climbs at a cost that follows the frontier, not n.
 template <typename T>
-__global__ void k_kick(Args<T> a, const int *choice, const T *alt, int r, unsigned long long *jumped) {
+__global__ void k_jump(Args<T> a, int r, unsigned epoch, unsigned *claim, unsigned long long *jumped) {
     const DevArena &A = a.A;
+    const int np = (int)(ld_cg(&a.ctrl->pull_ctr[r % 3]) & 0xffffffffu);
+    const int nq = (int)(ld_cg(&a.ctrl->push_ctr[r % 3]) & 0xffffffffu);
+    const int *pull = a.pull_items[r & 1], *push = a.push_items[r & 1];
     unsigned long long mine = 0;
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < A.n; v += gridDim.x * blockDim.x) {
-        int e = choice[v];
-        if (e < 0) continue;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np + nq; i += gridDim.x * blockDim.x) {
+        const int v = (i < np ? ld_cg(pull + i) : ld_cg(push + (i - np))) & 0x7fffffff;
         int cyc[KICK_LEN];
-        int len = 0, x = v;
-        bool ok = true;
+        T alts[KICK_LEN];
+        int len = 0, x = v, lo = v;
         long long wsum = 0;
-        do {
-            if (len == KICK_LEN || e < 0) {
-                ok = false;
-                break;
-            }
-            cyc[len++] = e;
+        bool closed = false;
+        while (len < KICK_LEN) {
+            int e;
+            T al;
+            if (!choice_of<T>(a, x, e, al)) break;
+            cyc[len] = e;
+            alts[len] = al;
+            ++len;
             wsum += wmap(__ldg(A.w + e), a.W);
             x = __ldg(A.col + e);
-            if (x < v) {  // the cycle, if any, is the smaller id's to jump
-                ok = false;
+            if (x == v) {
+                closed = true;
                 break;
             }
-            e = x == v ? 0 : choice[x];
-        } while (x != v);
-        if (!ok || wsum >= 0) continue;
+            lo = min(lo, x);
+        }
+        if (!closed || wsum >= 0) continue;
+        if (atomicExch(claim + lo, epoch) == epoch) continue;  // jumped from another entry
         // greatest solution around the cycle, from TOP: two backward laps
         T xv[KICK_LEN];
-        for (int i = 0; i < len; ++i) xv[i] = Cred<T>::TOP;
+        for (int k = 0; k < len; ++k) xv[k] = Cred<T>::TOP;
         for (int lap = 0; lap < 2; ++lap) {
-            for (int i = len - 1; i >= 0; --i) {
-                const int ce = cyc[i];
-                const int cv = i == 0 ? v : __ldg(A.col + cyc[i - 1]);
-                T val = ominus<T>(xv[i + 1 == len ? 0 : i + 1], wmap(__ldg(A.w + ce), a.W), a.W.C);
+            for (int k = len - 1; k >= 0; --k) {
+                const int cv = k == 0 ? v : __ldg(A.col + cyc[k - 1]);
+                T val = ominus<T>(xv[k + 1 == len ? 0 : k + 1], wmap(__ldg(A.w + cyc[k]), a.W), a.W.C);
                 const bool p1 = ((__ldg(A.owner_bits + (cv >> 5)) >> (cv & 31)) & 1u) ^ a.inv;
-                if (!p1) val = min(val, alt[cv]);
-                xv[i] = val;
+                if (!p1) val = min(val, alts[k]);
+                xv[k] = val;
             }
         }
-        for (int i = 0; i < len; ++i) {
-            const int cv = i == 0 ? v : __ldg(A.col + cyc[i - 1]);
-            if (!(xv[i] > ld_cg(a.f + cv))) continue;
-            if (!(xv[i] > atomicMax(a.f + cv, xv[i]))) continue;
+        for (int k = 0; k < len; ++k) {
+            const int cv = k == 0 ? v : __ldg(A.col + cyc[k - 1]);
+            if (!(xv[k] > ld_cg(a.f + cv))) continue;
+            if (!(xv[k] > atomicMax(a.f + cv, xv[k]))) continue;
             ++mine;
             const int work = __ldg(A.rrow_ptr + cv + 1) - __ldg(A.rrow_ptr + cv);
             const unsigned bit = 1u << (cv & 31);
@@ -1463,22 +1466,35 @@ struct SolveMem {
     bool fixed = false;     // laid over the allocation-free array
     bool in_place = false;  // sb's credit array is the caller's output buffer
     long long attempt_only = 0;  // > 0: only a first attempt of this many rounds (EG_ERR_BUDGET if unfinished)
-    int *kick_choice = nullptr;  // cycle jumps: each vertex's current choice (edge id),
-    void *kick_alt = nullptr;    //   a player-0 vertex's best other option (credit width of the phase),
+    unsigned *kick_claim = nullptr;  // cycle jumps: the epoch each vertex's cycle was last jumped in,
+    unsigned *kick_epoch = nullptr;  //   the epoch counter of that array (host),
     unsigned long long *kick_jumps = nullptr;  //   and the count of vertices raised
 };
 
-// The scratch of the cycle jumps of an allocating solve (allocated on first use).
-static eg_status kick_memory(eg_arena *ar, SolveMem &m) {
-    if (m.kick_choice) return EG_OK;
-    if (!ar->kick_block) {
-        const size_t o_alt = align_up((size_t)ar->n * 4), o_cnt = o_alt + align_up((size_t)ar->n * 8);
-        EG_CUDA_TRY(cudaMalloc(&ar->kick_block, o_cnt + 256));
+// Next epoch of a claim array; on wrap-around the array is cleared (0 is
+// never an epoch).
+static eg_status next_epoch(unsigned *claim, unsigned *epoch, long long n, cudaStream_t s, unsigned &out) {
+    if (++*epoch == 0) {
+        EG_CUDA_TRY(cudaMemsetAsync(claim, 0, (size_t)n * 4, s));
+        *epoch = 1;
     }
-    char *b = (char *)ar->kick_block;
-    m.kick_choice = (int *)b;
-    m.kick_alt = b + align_up((size_t)ar->n * 4);
-    m.kick_jumps = (unsigned long long *)(b + align_up((size_t)ar->n * 4) + align_up((size_t)ar->n * 8));
+    out = *epoch;
+    return EG_OK;
+}
+
+// The scratch of the cycle jumps of an allocating solve (allocated and
+// cleared on first use): a claim epoch per vertex and a counter.
+static eg_status kick_memory(eg_arena *ar, SolveMem &m) {
+    if (m.kick_claim) return EG_OK;
+    const size_t o_cnt = align_up((size_t)ar->n * 4);
+    if (!ar->kick_block) {
+        EG_CUDA_TRY(cudaMalloc(&ar->kick_block, o_cnt + 256));
+        EG_CUDA_TRY(cudaMemset(ar->kick_block, 0, o_cnt + 256));
+        ar->kick_epoch = 0;
+    }
+    m.kick_claim = (unsigned *)ar->kick_block;
+    m.kick_epoch = &ar->kick_epoch;
+    m.kick_jumps = (unsigned long long *)((char *)ar->kick_block + o_cnt);
     return EG_OK;
 }
 
@@ -1527,6 +1543,7 @@ static eg_status run_phase(eg_arena *ar, SolveMem &m, StateBuffers &sb, const We
         return EG_OK;
     }
     if ((rc = kick_memory(ar, m)) != EG_OK) return rc;
+    const int sms = num_sms(ar->device);
     EG_CUDA_TRY(cudaMemsetAsync(m.kick_jumps, 0, sizeof(unsigned long long), s));
     EG_CUDA_TRY(cudaEventRecord(ar->ev0, s));
     Launch Ls = L;
@@ -1536,7 +1553,6 @@ static eg_status run_phase(eg_arena *ar, SolveMem &m, StateBuffers &sb, const We
     const InstTable none{1, 0, nullptr, nullptr, nullptr, nullptr, nullptr};
     rc = enqueue_solve<false, T>(ar->d, W, none, ar->n, sb, Ls, ar->device, s, ar->evk, &a, &blocks);
     if (rc != EG_OK) return rc;
-    const int kb = (int)std::min<long long>((ar->n + 255) / 256, (long long)num_sms(ar->device) * 8);
     const Ctrl *hc = (const Ctrl *)ar->host_ctrl;
     bool budget = false;
     for (;;) {
@@ -1544,13 +1560,16 @@ static eg_status run_phase(eg_arena *ar, SolveMem &m, StateBuffers &sb, const We
         EG_CUDA_TRY(cudaStreamSynchronize(s));
         if (hc->status != DEV_OK) break;
         const long long r = hc->r_next;
-        if ((hc->pull_ctr[r % 3] & 0xffffffffu) == 0 && (hc->push_ctr[r % 3] & 0xffffffffu) == 0) break;
+        const long long entries = (long long)(hc->pull_ctr[r % 3] & 0xffffffffu) + (hc->push_ctr[r % 3] & 0xffffffffu);
+        if (entries == 0) break;
         if (L.max_rounds > 0 && r >= L.max_rounds) {
             budget = true;
             break;
         }
-        k_policy<T><<<kb, 256, 0, s>>>(a, m.kick_choice, (T *)m.kick_alt);
-        k_kick<T><<<kb, 256, 0, s>>>(a, m.kick_choice, (const T *)m.kick_alt, (int)r, m.kick_jumps);
+        unsigned epoch = 0;
+        if ((rc = next_epoch(m.kick_claim, m.kick_epoch, ar->n, s, epoch)) != EG_OK) return rc;
+        const int jb = (int)std::min<long long>((entries + 255) / 256, (long long)sms * 8);
+        k_jump<T><<<jb, 256, 0, s>>>(a, (int)r, epoch, m.kick_claim, m.kick_jumps);
         EG_CUDA_TRY(cudaGetLastError());
         a.r0 = r;
         a.max_rounds = L.max_rounds > 0 ? std::min(r + R, L.max_rounds) : r + R;
@@ -2656,17 +2675,16 @@ constexpr size_t NOALLOC_WORDS = (size_t)(NOALLOC_MAX_N + 31) / 32;
 constexpr size_t noalloc_up(size_t x) { return (x + 255) & ~size_t(255); }
 // layout: 8 lists of n ints, 7 bitmaps (5 of the solve state, the proven
 // player-0 and player-1 vertices), n partial minima (int64), n counts, the
-// int64 credits of the dual lifts, the cycle jumps' choices (n ints) and
-// alternatives (n int64), control block, counters (bound accumulators,
-// trial counts, vertices jumped)
+// int64 credits of the dual lifts, the cycle jumps' claim epochs (n ints),
+// control block, counters (bound accumulators, trial counts, vertices
+// jumped)
 constexpr size_t NA_LISTS = 0;
 constexpr size_t NA_BITS = NA_LISTS + 8 * noalloc_up((size_t)NOALLOC_MAX_N * 4);
 constexpr size_t NA_ACC = NA_BITS + 7 * noalloc_up(NOALLOC_WORDS * 4);
 constexpr size_t NA_DONE = NA_ACC + noalloc_up((size_t)NOALLOC_MAX_N * 8);
 constexpr size_t NA_DUAL = NA_DONE + noalloc_up((size_t)NOALLOC_MAX_N * 4);
-constexpr size_t NA_KCHOICE = NA_DUAL + noalloc_up((size_t)NOALLOC_MAX_N * 8);
-constexpr size_t NA_KALT = NA_KCHOICE + noalloc_up((size_t)NOALLOC_MAX_N * 4);
-constexpr size_t NA_CTRL = NA_KALT + noalloc_up((size_t)NOALLOC_MAX_N * 8);
+constexpr size_t NA_KCLAIM = NA_DUAL + noalloc_up((size_t)NOALLOC_MAX_N * 8);
+constexpr size_t NA_CTRL = NA_KCLAIM + noalloc_up((size_t)NOALLOC_MAX_N * 4);
 constexpr size_t NA_COUNT = NA_CTRL + noalloc_up(sizeof(Ctrl));
 constexpr size_t NA_BYTES = NA_COUNT + 256;
 
@@ -2684,6 +2702,9 @@ struct ScratchAddr {
 };
 static ScratchAddr g_noalloc_addr[64];
 static std::mutex g_noalloc_mu;
+// epoch counters of the claim array in g_noalloc_scratch, per device (the
+// array starts zeroed when the library loads; 0 is never an epoch)
+static unsigned g_noalloc_epoch[64];
 
 typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
 typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
@@ -2826,8 +2847,8 @@ static eg_status solve_noalloc(eg_arena *ar, int credit_bits, long long scale, l
     m.cert_w0 = (unsigned *)(base + NA_BITS + 5 * noalloc_up(words * 4));
     m.cert_w1 = (unsigned *)(base + NA_BITS + 6 * noalloc_up(words * 4));
     m.aux = dcount + 2;
-    m.kick_choice = (int *)(base + NA_KCHOICE);
-    m.kick_alt = base + NA_KALT;
+    m.kick_claim = (unsigned *)(base + NA_KCLAIM);
+    m.kick_epoch = &g_noalloc_epoch[device];
     m.kick_jumps = dcount + 4;
     m.fixed = true;
     m.in_place = true;

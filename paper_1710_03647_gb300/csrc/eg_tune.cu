@@ -259,7 +259,7 @@ static eg_status search(eg_arena *ar, RunFn run, void *ctx, cudaStream_t s, int 
     const int bps[] = {1, 2, 3, 0};
     const int cc[] = {2, 4, 8, 16};
     const int dk[] = {1, 2, 4, 8};
-    const int ca[] = {4, 8, 16, 32};
+    const int ca[] = {0, 4, 8, 16, 32};
     const int kr[] = {0, 1, 2, 4, 8};
     // the trial settings first: they change the number of rounds most
     const int order[] = {6, 3, 5, 0, 1, 2, 4};
@@ -272,7 +272,7 @@ static eg_status search(eg_arena *ar, RunFn run, void *ctx, cudaStream_t s, int 
                           : dim == 5 ? dk
                           : dim == 6 ? kr
                                      : ca;
-        const int nv = dim == 0 ? 6 : (dim == 1 || dim == 6) ? 5 : 4;
+        const int nv = dim == 0 ? 6 : (dim == 1 || dim == 4 || dim == 6) ? 5 : 4;
         for (int k = 0; k < nv; ++k) {
             if (solves + reps > max_solves) break;
             Settings c = best;
