@@ -252,16 +252,25 @@ def golden(name):
     return json.load(open(path)) if os.path.exists(path) else None
 
 
-def traffic_record(name):
-    """DRAM bytes per fixpoint launch from the committed ncu record, or None
-    when the kernel sources changed since it was taken."""
+def traffic_record(name, settings=None):
+    """DRAM bytes per solve from the committed ncu record, or None when the
+    kernel sources changed since it was taken or the record was taken with
+    other launch settings than `settings` (the ones timed)."""
     prof = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(prof):
         return None
     rec = json.load(open(prof))
     if rec.get("kernel_source_sha256") != kernel_source_hash():
         return None
-    return rec.get("dram_bytes_per_solve", rec.get("dram_bytes_per_launch"))
+    if settings is not None and any(rec.get("settings", {}).get(k) != v for k, v in settings.items()):
+        return None
+    return rec.get("dram_bytes_per_solve")
+
+
+SETTING_KEYS = ("local_windows", "local_maxdeg", "blocks_per_sm", "cap_certify", "certify_after", "dual_k",
+                "kick_rounds")
+DEFAULT_SETTINGS = dict(local_windows=64, local_maxdeg=64, blocks_per_sm=0, cap_certify=4, certify_after=8, dual_k=4,
+                        kick_rounds=2)
 
 
 def rmat_context(eg, gen, torch, dev, stream, flush, plain_start=True, tune=True, scc=True):
@@ -302,7 +311,10 @@ def rmat_context(eg, gen, torch, dev, stream, flush, plain_start=True, tune=True
              "rounds": res[-1][1]["rounds"], "relaxations_per_solve": res[-1][1]["relaxations"],
              "roofline": {"bound": "hbm", "achieved": bytes_alg / (fix_ms * 1e-3) / 1e9, "peak": peak,
                           "unit": "GB/s", "frac": bytes_alg / (fix_ms * 1e-3) / 1e9 / peak, "peak_kind": peak_kind,
-                          "traffic": traffic_record("fixpoint_rmat20_traffic.json"), "kernel": "k_fixpoint"},
+                          "traffic": traffic_record("fixpoint_rmat20_traffic.json",
+                                                    {k: tuning[k] for k in SETTING_KEYS} if tuning
+                                                    else dict(DEFAULT_SETTINGS)),
+                          "kernel": "k_fixpoint"},
              "oracle": None, "settings": "autotuned (eg_autotune)" if tuning else "defaults", "tuning": tuning}
     if g:
         out_d["oracle"] = {"time_to_fixpoint_s": g["oracle_seconds"], "route": "Algorithm 1 with cap C, 1 thread",
@@ -589,7 +601,7 @@ def main():
 
         t0 = time.perf_counter()
         with tempfile.TemporaryDirectory() as td:
-            tuning = eg.eg_autotune(arena.handle, bits, 1, 0, os.path.join(td, "plans.jsonl"), max_solves=40)
+            tuning = eg.eg_autotune(arena.handle, bits, 1, 0, os.path.join(td, "plans.jsonl"), max_solves=60)
         tuning["search_s"] = time.perf_counter() - t0
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -631,7 +643,8 @@ def main():
     bytes_alg = sum(algorithmic_bytes(x, s) for x in stats)
     peak, peak_kind = peaks()
     achieved = bytes_alg / (fix_ms * 1e-3) / 1e9
-    traffic = traffic_record(f"fixpoint_grid{side}_traffic.json")
+    settings = {k: tuning[k] for k in SETTING_KEYS} if tuning else dict(DEFAULT_SETTINGS)
+    traffic = traffic_record(f"fixpoint_grid{side}_traffic.json", settings)
 
     # end to end through the public API: the arena from pinned host arrays
     # (eg_create copies them and builds the reverse CSR on the device), one
@@ -744,6 +757,7 @@ def main():
                    "l2": "flushed between steps (512 MiB write); arena and state exceed L2"},
         "all_exact": ok,
         "settings": "autotuned (eg_autotune)" if tuning else "defaults",
+        "launch_settings": settings,
         "tuning": tuning,
         "time_to_fixpoint_ms": statistics.median(step_ms),
         "oracle": oracle_ref,

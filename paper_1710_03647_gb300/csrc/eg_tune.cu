@@ -261,8 +261,9 @@ static eg_status search(eg_arena *ar, RunFn run, void *ctx, cudaStream_t s, int 
     const int dk[] = {1, 2, 4, 8};
     const int ca[] = {0, 4, 8, 16, 32};
     const int kr[] = {0, 1, 2, 4, 8};
-    // the trial settings first: they change the number of rounds most
-    const int order[] = {6, 3, 5, 0, 1, 2, 4};
+    // the route's settings first (the first attempt, the jumps' slices, the
+    // trials' cap and K): they change the work most
+    const int order[] = {4, 6, 3, 5, 0, 1, 2};
     for (int dim : order) {
         if ((dim == 3 || dim == 4 || dim == 5 || dim == 6) && !trials_matter) continue;
         const int *vals = dim == 0   ? lw

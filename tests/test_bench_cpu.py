@@ -28,12 +28,14 @@ def test_comment_edit_keeps_the_hash_code_edit_changes_it():
     assert norm("// a\n// b\n// c\n" + code) == norm(code)
 
 
-def test_traffic_record_names_a_kernel_hash_and_bytes():
-    p = os.path.join(bench.ROOT, "profiles", "fixpoint_rmat20_traffic.json")
-    rec = json.load(open(p))
-    assert rec["dram_bytes_per_launch"] == rec["dram_bytes_read"] + rec["dram_bytes_write"] > 0
-    assert len(rec["kernel_source_sha256"]) == 64
-    assert rec["command"].startswith("ncu ") and "--clock-control none" in rec["command"]
+def test_traffic_records_name_a_kernel_hash_and_bytes():
+    for name, key in (("fixpoint_grid4000_traffic.json", "dram_bytes_per_solve"),
+                      ("fixpoint_rmat20_traffic.json", "dram_bytes_per_solve")):
+        rec = json.load(open(os.path.join(bench.ROOT, "profiles", name)))
+        assert rec[key] == rec["dram_bytes_read"] + rec["dram_bytes_write"] > 0
+        assert len(rec["kernel_source_sha256"]) == 64
+        assert rec["command"].startswith("ncu ") and "--clock-control none" in rec["command"]
+
 
 
 def test_clock_summary_prefers_samples_inside_the_timed_window():
