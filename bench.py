@@ -268,9 +268,9 @@ def traffic_record(name, settings=None):
 
 
 SETTING_KEYS = ("local_windows", "local_maxdeg", "blocks_per_sm", "cap_certify", "certify_after", "dual_k",
-                "kick_rounds")
+                "kick_rounds", "sweeps", "chunk_edges")
 DEFAULT_SETTINGS = dict(local_windows=64, local_maxdeg=64, blocks_per_sm=0, cap_certify=4, certify_after=8, dual_k=4,
-                        kick_rounds=2)
+                        kick_rounds=2, sweeps=0, chunk_edges=1024)
 
 
 def rmat_context(eg, gen, torch, dev, stream, flush, plain_start=True, tune=True, scc=True):
@@ -289,7 +289,7 @@ def rmat_context(eg, gen, torch, dev, stream, flush, plain_start=True, tune=True
         import tempfile
 
         with tempfile.TemporaryDirectory() as td:
-            tuning = eg.eg_autotune(arena.handle, bits, 1, 0, os.path.join(td, "plans.jsonl"), max_solves=60)
+            tuning = eg.eg_autotune(arena.handle, bits, 1, 0, os.path.join(td, "plans.jsonl"), max_solves=80)
     res = []
     for k in range(10):
         with torch.cuda.stream(stream):
@@ -375,7 +375,7 @@ def batch_games(eg, gen, torch, dev, stream, count, tune=True):
         import tempfile
 
         with tempfile.TemporaryDirectory() as td:
-            tuning = eg.eg_plan_autotune(plan, os.path.join(td, "plans.jsonl"), max_solves=30)
+            tuning = eg.eg_plan_autotune(plan, os.path.join(td, "plans.jsonl"), max_solves=80)
     bms = []
     for _ in range(3):
         b, e = ev_pair()
@@ -601,7 +601,7 @@ def main():
 
         t0 = time.perf_counter()
         with tempfile.TemporaryDirectory() as td:
-            tuning = eg.eg_autotune(arena.handle, bits, 1, 0, os.path.join(td, "plans.jsonl"), max_solves=60)
+            tuning = eg.eg_autotune(arena.handle, bits, 1, 0, os.path.join(td, "plans.jsonl"), max_solves=80)
         tuning["search_s"] = time.perf_counter() - t0
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]

@@ -246,6 +246,21 @@ eg_status eg_strategy(eg_arena *arena, int32_t credit_bits, int64_t w_scale, int
  *     trials).  A condensation of a single level (one component, as a
  *     road-like grid has) takes the default route instead.
  *     eg_solve_credit_noalloc ignores the option.
+ *   EG_OPT_CHUNK_EDGES (default 1024): a round whose worklist holds more than
+ *     this many edges per warp of the fixpoint kernel is worked in chunks of
+ *     this many edges that the warps take in list order, so the whole grid
+ *     sweeps the list together and the credits its gathers reach stay in L2;
+ *     a shorter list is cut into one equal piece per warp.  0 always cuts one
+ *     piece per warp.
+ *   EG_OPT_SWEEPS (default 0, at most 1024): dense sweeps before the
+ *     worklist rounds of each fixpoint launch (not the levels of an
+ *     SCC-ordered solve).  A sweep raises every credit, in index order and in
+ *     place, to its lift over all its edges -- coalesced reads, no atomics --
+ *     and the last sweep's raised credits start the worklist rounds.  Lifts
+ *     from below stay below the least fixpoint, so the result is unchanged;
+ *     sweeps pay off where the first rounds touch most edges anyway.  Their
+ *     edge evaluations count in the relaxations; they are not rounds and
+ *     max_rounds does not bound them.
  *
  * EG_ERR_INVALID for an unknown option or a value out of range.
  */
@@ -261,6 +276,8 @@ eg_status eg_strategy(eg_arena *arena, int32_t credit_bits, int64_t w_scale, int
 #define EG_OPT_SCC_ORDER 10
 #define EG_OPT_DUAL_K 11
 #define EG_OPT_KICK_ROUNDS 12
+#define EG_OPT_CHUNK_EDGES 13
+#define EG_OPT_SWEEPS 14
 eg_status eg_set_option(eg_arena *arena, int32_t option, int64_t value);
 
 /*
@@ -380,6 +397,7 @@ typedef struct eg_tuning {
     int32_t local_windows, local_maxdeg, blocks_per_sm, cap_certify;
     int64_t certify_after;
     int32_t dual_k, kick_rounds;
+    int32_t sweeps, chunk_edges;
     double default_ms;   /* time to the fixpoint with the settings the search started from (-1: cached) */
     double tuned_ms;     /* with the chosen settings (the cached figure when from_cache) */
     int32_t solves;      /* runs timed by this call */

@@ -33,7 +33,7 @@ def main(argv=None) -> None:
     ap.add_argument("--max-rounds", type=int, default=0)
     ap.add_argument("--repeat", type=int, default=1)
     for opt in ("local-windows", "local-maxdeg", "warm-start", "cap-certify", "certify-after", "dual-k",
-                "blocks-per-sm", "scc-order"):
+                "blocks-per-sm", "scc-order", "kick-rounds", "sweeps", "chunk-edges"):
         ap.add_argument("--" + opt, type=int, default=None)
     args = ap.parse_args(argv)
     if args.workload == "batch":
@@ -50,7 +50,8 @@ def main(argv=None) -> None:
     with eg.Arena(a) as arena:
         arena.tune(local_windows=args.local_windows, local_maxdeg=args.local_maxdeg, warm_start=args.warm_start,
                    cap_certify=args.cap_certify, certify_after=args.certify_after, dual_k=args.dual_k,
-                   blocks_per_sm=args.blocks_per_sm, scc_order=args.scc_order)
+                   blocks_per_sm=args.blocks_per_sm, scc_order=args.scc_order, kick_rounds=args.kick_rounds,
+                   sweeps=args.sweeps, chunk_edges=args.chunk_edges)
         out = np.empty(a.n, dtype=np.int32 if args.bits == 32 else np.int64)
         for _ in range(args.repeat):
             rc, st = eg.eg_solve_credit(arena.handle, args.bits, 1, 0, out, max_rounds=args.max_rounds,
@@ -65,7 +66,8 @@ def batch(args) -> None:
     with eg.Arena(gen.Arena(n, row_ptr, col, w, owner_bits, "batch")) as arena:
         arena.tune(local_windows=args.local_windows, local_maxdeg=args.local_maxdeg, warm_start=args.warm_start,
                    cap_certify=args.cap_certify, certify_after=args.certify_after, dual_k=args.dual_k,
-                   blocks_per_sm=args.blocks_per_sm)
+                   blocks_per_sm=args.blocks_per_sm, kick_rounds=args.kick_rounds, sweeps=args.sweeps,
+                   chunk_edges=args.chunk_edges)
         eg.eg_set_parts(arena.handle, part_ptr)
         with eg.Plan(arena.handle, args.games, credit_bits=args.bits) as plan:
             for _ in range(args.repeat):

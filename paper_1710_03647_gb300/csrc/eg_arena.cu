@@ -687,6 +687,14 @@ eg_status eg_set_option(eg_arena *arena, int32_t option, int64_t value) {
     case EG_OPT_CERTIFY_AFTER: arena->certify_after = value; break;
     case EG_OPT_BLOCKS_PER_SM: arena->blocks_per_sm = (int)value; break;
     case EG_OPT_KICK_ROUNDS: arena->kick_rounds = value; break;
+    case EG_OPT_CHUNK_EDGES: arena->chunk_edges = (int)value; break;
+    case EG_OPT_SWEEPS:
+        if (value > 1024) {
+            eg::set_error("EG_OPT_SWEEPS takes at most 1024");
+            return EG_ERR_INVALID;
+        }
+        arena->sweeps = (int)value;
+        break;
     case EG_OPT_DUAL_K:
         if (value < 1) {
             eg::set_error("EG_OPT_DUAL_K takes at least 1");

@@ -37,6 +37,7 @@ struct Ctrl {
     unsigned stop_flag;  // a slice of a resident solve ends after this round (doorbell seen)
     unsigned long long rounds, lifts, pushes, relax, enqueues, seeded;
     long long r_next;    // round a resident solve resumes at
+    unsigned pull_take[3], push_take[3];  // chunks of round r's lists taken so far (slot r % 3)
 };
 
 // Read-only arena data on the device (int32 offsets: m < 2^31).
@@ -100,6 +101,8 @@ struct eg_arena {
     void *host_ctrl = nullptr;  // pinned copy of Ctrl
     int local_windows = 64;     // per-warp local worklist budget per round (0 disables chaining)
     int local_maxdeg = 64;      // largest degree of a vertex handled through the local worklist
+    int chunk_edges = 1024;     // edges per chunk of a round's list that spans more per warp (0: one chunk per warp)
+    int sweeps = 0;             // dense sweeps (in-place lifts of every credit) before the worklist rounds
     int warm_start = 1;         // TOP on player-1 negative cycles of length <= 2 before lifting
     long long seed_max_pairs = 4096;
     int use_graph = 1;                // batched solves replay a captured graph
@@ -162,6 +165,7 @@ struct Resident {
     long long *host_tab = nullptr;  // pinned staging of the slot tables (scale, shift, C per slot)
     long long r = 0;                // next round
     int local_windows = 64, local_maxdeg = 64;
+    int chunk_edges = 1024;  // edges per chunk of a long list (0: one chunk per warp)
     long long seed_max_pairs = 4096;
 };
 eg_status resident_create(Resident &R, int device, int cap, int slots, cudaStream_t s);

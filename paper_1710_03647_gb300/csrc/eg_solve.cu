@@ -55,6 +55,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <climits>
 #include <mutex>
 #include <vector>
 
@@ -87,6 +88,8 @@ struct InstTable {
     const long long *C;
     const int *inst_id;  // non-null: instance of each credit (resident solves)
     const int *active;   // non-null: instances with active[i] == 0 are left as they are
+    const int *lut = nullptr;  // non-null: instance of credit b << lut_shift, for every b; a block of
+    int lut_shift = 0;         //   2^lut_shift credits is no longer than the shortest instance
 };
 
 template <typename T>
@@ -115,6 +118,7 @@ struct Args {
     const volatile unsigned *doorbell;  // resident solves: host-set flag that ends the slice
     int local_windows;  // per-warp budget of local windows per round (0: no chaining)
     int local_maxdeg;   // largest degree a vertex may have to be chained locally
+    int chunk;          // edges per chunk of a list with more than that per warp (0: one chunk per warp)
     unsigned long long wait_ns;  // limit of each grid-barrier wait
     const int *level;  // SCC-ordered solves: topological level of each vertex (or null)
     int cur_level;     // the level being solved; predecessors above it are left for later
@@ -135,6 +139,11 @@ __device__ __forceinline__ long long wmapv(int w, const View &v) { return v.scal
 __device__ __forceinline__ int inst_of(const InstTable &I, int g) {
     if (I.inst_id) return __ldg(I.inst_id + g);
     if (I.uniform_n > 0) return g / I.uniform_n;
+    if (I.lut) {  // the instance of the block's first credit, or the next one
+        int i = __ldg(I.lut + (g >> I.lut_shift));
+        while (__ldg(I.fbase + i + 1) <= g) ++i;
+        return i;
+    }
     int lo = 0, hi = I.count;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
@@ -207,13 +216,12 @@ __global__ void k_fill(T *p, long long n, T v) {
 // (Lemma "EGcycles" with memoryless determinacy, Sec. 3).  Its least-EPM
 // value is TOP, so starting it at TOP stays below the least fixpoint.
 // Looked for: negative self-loops and 2-cycles u -> t -> u with t a player-1
-// vertex.  A vertex whose out- and in-degree are both at most
-// SEED_LANE_DEG is checked by one lane alone (its in-edges held in registers,
-// every load independent); a larger one by the whole warp, which compares
-// each out-edge (u, t) with each in-edge (s, u) for s == t.  Vertices with
-// out-degree x in-degree above max_pairs are skipped (the warm start is
-// optional, missing a cycle only costs time).
-constexpr int SEED_LANE_DEG = 8;
+// vertex, by comparing each out-edge (u, t) with each in-edge (s, u) for
+// s == t.  A vertex with at most SEED_LANE_EDGES in- and out-edges together
+// is checked by one lane alone, over its own rows; a larger one by the whole
+// warp.  Vertices with out-degree x in-degree above max_pairs are skipped
+// (the warm start is optional, missing a cycle only costs time).
+constexpr int SEED_LANE_EDGES = 64;
 
 template <bool MULTI, typename T>
 __global__ void k_seed(Args<T> a, long long max_pairs, unsigned *seed_bits, unsigned long long *count, int g0,
@@ -239,31 +247,38 @@ __global__ void k_seed(Args<T> a, long long max_pairs, unsigned *seed_bits, unsi
                 mine = (long long)(oe - ob) * (long long)(ie - ib) <= max_pairs;
             }
         }
-        const bool small = mine && oe - ob <= SEED_LANE_DEG && ie - ib <= SEED_LANE_DEG;
+        const bool small = mine && (oe - ob) + (ie - ib) <= SEED_LANE_EDGES;
         bool found = false;
         if (small) {
-            unsigned sv[SEED_LANE_DEG];
-            long long ws[SEED_LANE_DEG];
-#pragma unroll
-            for (int j = 0; j < SEED_LANE_DEG; ++j) {
-                sv[j] = 0;
-                ws[j] = 0;
-                if (ib + j < ie) {
-                    sv[j] = __ldg(A.rcol + ib + j);
-                    ws[j] = wmapv(__ldg(A.rw + ib + j), vw);
+            // the lane alone: a 128-bit filter of its player-1 predecessors
+            // (two bits per id, from its low and next 7 bits) rejects almost
+            // every out-edge with one test; the in-row is searched only
+            // where the filter matches
+            unsigned long long filt[2] = {0, 0};
+#pragma unroll 4
+            for (int j = ib; j < ie; ++j) {
+                const unsigned sj = __ldg(A.rcol + j);
+                if (((sj & P1_FLAG) != 0) != (a.inv != 0)) {
+                    const unsigned h1 = sj & 127u, h2 = (sj >> 7) & 127u;
+                    filt[h1 >> 6] |= 1ull << (h1 & 63u);
+                    filt[h2 >> 6] |= 1ull << (h2 & 63u);
                 }
             }
-#pragma unroll
-            for (int k = 0; k < SEED_LANE_DEG; ++k) {
-                if (ob + k < oe) {
-                    const int t = __ldg(A.col + ob + k);
-                    const long long wt = wmapv(__ldg(A.w + ob + k), vw);
-                    if (t == u && wt < 0) found = true;  // negative self-loop
-#pragma unroll
-                    for (int j = 0; j < SEED_LANE_DEG; ++j)
-                        if (ib + j < ie && ((sv[j] & P1_FLAG) != 0) != (a.inv != 0) &&
-                            (int)(sv[j] & 0x7fffffffu) == t && t != u && wt + ws[j] < 0)
+#pragma unroll 4
+            for (int k = ob; k < oe; ++k) {
+                const int t = __ldg(A.col + k);
+                const unsigned h1 = (unsigned)t & 127u, h2 = ((unsigned)t >> 7) & 127u;
+                const bool maybe = ((filt[h1 >> 6] >> (h1 & 63u)) & 1ull) && ((filt[h2 >> 6] >> (h2 & 63u)) & 1ull);
+                if (t == u) {
+                    if (wmapv(__ldg(A.w + k), vw) < 0) found = true;  // negative self-loop
+                } else if (maybe) {
+                    const long long wt = wmapv(__ldg(A.w + k), vw);
+                    for (int j = ib; j < ie; ++j) {
+                        const unsigned sj = __ldg(A.rcol + j);
+                        if ((int)(sj & 0x7fffffffu) == t && ((sj & P1_FLAG) != 0) != (a.inv != 0) &&
+                            wt + wmapv(__ldg(A.rw + j), vw) < 0)
                             found = true;
+                    }
                 }
             }
         }
@@ -326,7 +341,7 @@ __global__ void k_seed(Args<T> a, long long max_pairs, unsigned *seed_bits, unsi
 // vertices, and the warm-start ones (TOP), enter the push list of the first
 // round (list counter `slot`, buffer `buf`).  Credits [g0, g1) are set.
 template <bool MULTI, typename T>
-__global__ void __launch_bounds__(THREADS) k_init(Args<T> a, int g0, int g1, int slot, int buf) {
+__global__ void __launch_bounds__(THREADS) k_init(Args<T> a, int g0, int g1, int slot, int buf, int list) {
     const DevArena &A = a.A;
     const int nthreads = gridDim.x * blockDim.x;
     for (int base = g0 + blockIdx.x * blockDim.x; base < g1; base += nthreads) {
@@ -353,7 +368,7 @@ __global__ void __launch_bounds__(THREADS) k_init(Args<T> a, int g0, int g1, int
             work = __ldg(A.rrow_ptr + v + 1) - __ldg(A.rrow_ptr + v);
             want = !fz && f0 > T(0) && work > 0;
         }
-        warp_append(want, (unsigned)g, work, &a.ctrl->push_ctr[slot], a.push_items[buf], a.push_offs[buf]);
+        warp_append(list && want, (unsigned)g, work, &a.ctrl->push_ctr[slot], a.push_items[buf], a.push_offs[buf]);
     }
 }
 
@@ -500,6 +515,135 @@ __device__ __forceinline__ T pull_min(const Args<T> &a, int beg, int o, const Vi
     const T g = red[lane];
     __syncwarp();
     return g;
+}
+
+// ---------------------------------------------------------------------------
+// Dense sweeps before the worklist rounds.  One sweep evaluates the lift
+// delta(f, v) of every credit in index order and raises f(v) to it in place:
+// the minimum over v's edges of f(u) (-) w(v, u) for a player-0 vertex, the
+// maximum for a player-1 vertex (Sec. 3.1).  Each credit has a single writer
+// (its lane), so no atomics are needed, and a warp reads 32 consecutive rows
+// with coalesced loads.  The lift is monotone, so raising credits to it from
+// below, with successor credits read old or new, never passes the least
+// fixpoint (the chaotic iteration of Sec. 3.1's lifting).
+//
+// Only the last sweep builds the first round's push list: a credit it raised
+// joins the list.  A credit whose lift read a successor before that
+// successor rose in the last sweep has the successor on the list, and one
+// that read it before a rise in an earlier sweep read it again in a later
+// sweep; so after the rounds that follow, every credit is its own lift.
+// Warm-start credits at TOP and frozen credits (held at 0) are left alone.
+
+// Per owning lane, the lift over the warp's edges [0, stop): the minimum of
+// f(u) (-) w for a player-0 entry, the maximum for a player-1 entry (lanes
+// owning no edge get TOP or 0).  beg, o, vw as in pull_min; p1: the lane's
+// entry belongs to player 1.
+template <bool MULTI, typename T>
+__device__ __forceinline__ T sweep_lift(const Args<T> &a, int beg, int o, const View &vw, bool p1, int stop,
+                                        T *red) {
+    const int lane = lane_id();
+    red[lane] = p1 ? T(0) : Cred<T>::TOP;
+    __syncwarp();
+    for (int xb = 0; xb < stop; xb += 32) {
+        const int xl = xb + lane;
+        const bool act = xl < stop;
+        const int j = owner_lane(o, xl);
+        const int bj = __shfl_sync(FULL, beg, j);
+        const int oj = __shfl_sync(FULL, o, j);
+        const bool pj = __shfl_sync(FULL, p1, j);
+        const View vj = shfl_view<MULTI>(vw, j);
+        T t = pj ? T(0) : Cred<T>::TOP;
+        if (act) {
+            const int e = bj + (xl - oj);
+            const int u = __ldg(a.A.col + e) + vj.delta;
+            t = ominus<T>(ld_cg(a.f + u), wmapv(__ldg(a.A.w + e), vj), vj.C);
+        }
+        const int key = act ? j : 32 + lane;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const T ov = __shfl_up_sync(FULL, t, d);
+            const int ok = __shfl_up_sync(FULL, key, d);
+            if (lane >= d && ok == key) t = pj ? max(t, ov) : min(t, ov);
+        }
+        const int nk = __shfl_down_sync(FULL, key, 1);
+        if (act && (lane == 31 || nk != key)) red[j] = pj ? max(red[j], t) : min(red[j], t);
+        __syncwarp();
+    }
+    const T g = red[lane];
+    __syncwarp();
+    return g;
+}
+
+// Rows of at most this many edges are walked by one lane in a sweep.
+constexpr int SWEEP_LANE_DEG = 32;
+
+// One sweep over the credits [0, nf); with `last`, raised credits join the
+// push list of round 0 (list counter 0, buffer 0).
+template <bool MULTI, typename T>
+__global__ void __launch_bounds__(THREADS) k_sweep(Args<T> a, int last) {
+    __shared__ T red_all[WARPS][32];
+    T *red = red_all[threadIdx.x >> 5];
+    const DevArena &A = a.A;
+    const int lane = lane_id();
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    unsigned long long relax = 0, lifts = 0;
+    for (int base = gw * 32; base < a.nf; base += nw * 32) {
+        const int g = base + lane;
+        bool on = g < a.nf && in_active<MULTI>(a, g);
+        View vw = idle_view<MULTI>(a);
+        bool p1 = false;
+        int v = 0, beg = 0, work = 0;
+        T cur = T(0);
+        if (on) {
+            vw = view_of<MULTI>(a, g);
+            v = g - vw.delta;
+            const bool fz = a.frozen && ((__ldg(a.frozen + (g >> 5)) >> (g & 31)) & 1u);
+            cur = ld_cg(a.f + g);
+            on = !fz && cur != Cred<T>::TOP && vw.C >= 0;
+            p1 = ((__ldg(A.owner_bits + (v >> 5)) >> (v & 31)) & 1u) ^ a.inv;
+            if (on) {
+                beg = __ldg(A.row_ptr + v);
+                work = __ldg(A.row_ptr + v + 1) - beg;
+            }
+        }
+        // a light row is walked by its own lane (the rows of neighbouring
+        // credits share cache lines, and lanes exchange nothing); the heavy
+        // rows of the warp are walked by all its lanes together
+        const bool light = work <= SWEEP_LANE_DEG;
+        T res = p1 ? T(0) : Cred<T>::TOP;
+        if (light) {
+            const int *cp = A.col + beg;
+            const int *wp = A.w + beg;
+#pragma unroll 4
+            for (int k = 0; k < work; ++k) {
+                const T t = ominus<T>(ld_cg(a.f + (__ldg(cp + k) + vw.delta)), wmapv(__ldg(wp + k), vw), vw.C);
+                res = p1 ? max(res, t) : min(res, t);
+            }
+        }
+        int o;
+        const int heavy = warp_exclusive(light ? 0 : work, o);
+        if (heavy > 0) {
+            const T hr = sweep_lift<MULTI, T>(a, beg, o, vw, p1, heavy, red);
+            if (!light) res = hr;
+        }
+        bool rose = false;
+        if (work > 0 && res > cur) {
+            st_cg(a.f + g, res);
+            rose = true;
+        }
+        relax += __reduce_add_sync(FULL, (unsigned)work);
+        lifts += __popc(__ballot_sync(FULL, work > 0 && !p1));
+        if (last) {
+            const int pwork = rose ? __ldg(A.rrow_ptr + v + 1) - __ldg(A.rrow_ptr + v) : 0;
+            warp_append(rose && pwork > 0, (unsigned)g, pwork, &a.ctrl->push_ctr[0], a.push_items[0],
+                        a.push_offs[0]);
+        }
+    }
+    if (lane == 0 && relax) {
+        atomicAdd(&a.ctrl->relax, relax);
+        atomicAdd(&a.ctrl->lifts, lifts);
+    }
 }
 
 // Per-warp staging of list appends: entries collect in shared memory and
@@ -745,6 +889,40 @@ __device__ void drain_local(const Args<T> &a, int r, T *red, Local<T> &L) {
 }
 
 // ---------------------------------------------------------------------------
+// Work split of a round's list over the warps, in its edge coordinates
+// [0, total).  A list of at most `chunk` edges per warp is cut into one equal
+// piece per warp.  A longer one is cut into chunks of `chunk` edges that the
+// warps take in order, the first by warp id and the rest from the round's
+// take counter, so that the whole grid sweeps the list together: the credits
+// and rows its gathers reach (those of the vertices near the sweep, which in
+// a list built in vertex order are the same few games) stay in L2, where
+// with one piece per warp every warp would pull its own far part of the arena
+// through L2 at once.
+struct ChunkPlan {
+    long long first;   // the warp's first chunk
+    long long K;       // edges per chunk
+    long long nwarps;  // chunks handed out by warp id
+    bool dyn;          // further chunks come from the take counter
+};
+
+__device__ __forceinline__ ChunkPlan chunk_plan(int total, int chunk) {
+    ChunkPlan cp;
+    cp.nwarps = (long long)gridDim.x * WARPS;
+    cp.first = (long long)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    cp.dyn = chunk > 0 && (long long)total > cp.nwarps * chunk;
+    cp.K = cp.dyn ? max(chunk, 32) : max(32LL, ((long long)total + cp.nwarps - 1) / cp.nwarps);
+    return cp;
+}
+
+// The warp's next chunk; with the static split one past every list.
+__device__ __forceinline__ long long next_chunk(const ChunkPlan &cp, unsigned *take) {
+    if (!cp.dyn) return (long long)INT_MAX;
+    unsigned t = 0;
+    if (lane_id() == 0) t = atomicAdd(take, 1u);
+    return cp.nwarps + (long long)__shfl_sync(FULL, t, 0);
+}
+
+// ---------------------------------------------------------------------------
 // Pull phase: lift the player-0 vertices of the pull list of round r.
 template <bool MULTI, typename T>
 __device__ void pull_phase(const Args<T> &a, int r, T *red, Stager &out) {
@@ -758,60 +936,58 @@ __device__ void pull_phase(const Args<T> &a, int r, T *red, Stager &out) {
     unsigned *bits = a.bits_pull[r & 1];
     unsigned *bits_q = a.bits_push[r & 1];
 
-    const int nwarps = gridDim.x * WARPS;
-    const int gw = blockIdx.x * WARPS + (threadIdx.x >> 5);
-    const int K = max(32, (total + nwarps - 1) / nwarps);
-    const int lo = gw * K;
-    if (lo >= total) return;
-    const int hi = min(total, lo + K);
-
-    int i = warp_find(offs, cnt, lo);
-    int x = lo;
-    while (x < hi) {
-        const int ii = i + lane;
-        const bool valid = ii < cnt;
-        int g = 0, v = 0, o = total, oend = total, beg = 0;
-        View vw = idle_view<MULTI>(a);
-        if (valid) {
-            g = ld_cg(items + ii) & 0x7fffffff;
-            vw = view_of<MULTI>(a, g);
-            v = g - vw.delta;
-            o = ld_cg(offs + ii);
-            oend = ii + 1 < cnt ? ld_cg(offs + ii + 1) : total;
-            beg = __ldg(A.row_ptr + v);
-        }
-        const int stop = min(hi, __shfl_sync(FULL, oend, 31));
-        const T gmin = pull_min<MULTI, T>(a, beg, o, vw, x, stop, red);
-        // finish the lifts of this window's entries
-        bool changed = false;
-        int pwork = 0;
-        if (valid && o < stop && oend > x) {
-            if (o >= lo) atomicAnd(bits + (g >> 5), ~(1u << (g & 31)));  // consumed
-            const int seen = min(oend, stop) - max(o, x);
-            T res = gmin;
-            bool done = true;
-            if (seen != oend - o) {  // lift split across warps: merge partial minima
-                atomicMin(a.acc + g, gmin);
-                __threadfence();
-                const int before = atomicAdd(a.acc_done + g, seen);
-                done = before + seen == oend - o;
-                if (done) {
+    const ChunkPlan cp = chunk_plan(total, a.chunk);
+    for (long long c = cp.first; c * cp.K < total; c = next_chunk(cp, &a.ctrl->pull_take[r % 3])) {
+        const int lo = (int)(c * cp.K);
+        const int hi = (int)min((long long)total, c * cp.K + cp.K);
+        int i = warp_find(offs, cnt, lo);
+        int x = lo;
+        while (x < hi) {
+            const int ii = i + lane;
+            const bool valid = ii < cnt;
+            int g = 0, v = 0, o = total, oend = total, beg = 0;
+            View vw = idle_view<MULTI>(a);
+            if (valid) {
+                g = ld_cg(items + ii) & 0x7fffffff;
+                vw = view_of<MULTI>(a, g);
+                v = g - vw.delta;
+                o = ld_cg(offs + ii);
+                oend = ii + 1 < cnt ? ld_cg(offs + ii + 1) : total;
+                beg = __ldg(A.row_ptr + v);
+            }
+            const int stop = min(hi, __shfl_sync(FULL, oend, 31));
+            const T gmin = pull_min<MULTI, T>(a, beg, o, vw, x, stop, red);
+            // finish the lifts of this window's entries
+            bool changed = false;
+            int pwork = 0;
+            if (valid && o < stop && oend > x) {
+                if (o >= lo) atomicAnd(bits + (g >> 5), ~(1u << (g & 31)));  // consumed
+                const int seen = min(oend, stop) - max(o, x);
+                T res = gmin;
+                bool done = true;
+                if (seen != oend - o) {  // lift split across chunks: merge partial minima
+                    atomicMin(a.acc + g, gmin);
                     __threadfence();
-                    res = xchg(a.acc + g, Cred<T>::TOP);
-                    atomicExch(a.acc_done + g, 0);
+                    const int before = atomicAdd(a.acc_done + g, seen);
+                    done = before + seen == oend - o;
+                    if (done) {
+                        __threadfence();
+                        res = xchg(a.acc + g, Cred<T>::TOP);
+                        atomicExch(a.acc_done + g, 0);
+                    }
+                }
+                if (done && vw.C >= 0 && res > ld_cg(a.f + g) && res > atomicMax(a.f + g, res)) {
+                    pwork = __ldg(A.rrow_ptr + v + 1) - __ldg(A.rrow_ptr + v);
+                    if (pwork > 0) {
+                        const unsigned bit = 1u << (g & 31);
+                        changed = !(ld_cg(bits_q + (g >> 5)) & bit) && !(atomicOr(bits_q + (g >> 5), bit) & bit);
+                    }
                 }
             }
-            if (done && vw.C >= 0 && res > ld_cg(a.f + g) && res > atomicMax(a.f + g, res)) {
-                pwork = __ldg(A.rrow_ptr + v + 1) - __ldg(A.rrow_ptr + v);
-                if (pwork > 0) {
-                    const unsigned bit = 1u << (g & 31);
-                    changed = !(ld_cg(bits_q + (g >> 5)) & bit) && !(atomicOr(bits_q + (g >> 5), bit) & bit);
-                }
-            }
+            stage_append(out, changed, (unsigned)g, pwork);
+            x = stop;
+            i += 32;
         }
-        stage_append(out, changed, (unsigned)g, pwork);
-        x = stop;
-        i += 32;
     }
 }
 
@@ -829,10 +1005,6 @@ __device__ void push_phase(const Args<T> &a, int r, T *red, Local<T> &L) {
     const int *offs = a.push_offs[r & 1];
     unsigned *bits_cur = a.bits_push[r & 1];
 
-    const int nwarps = gridDim.x * WARPS;
-    const int gw = blockIdx.x * WARPS + (threadIdx.x >> 5);
-    const int K = max(32, (total + nwarps - 1) / nwarps);
-    const int lo = gw * K;
     L.top = 0;
     L.on = a.local_windows > 0;
     L.next_pull.n = 0;
@@ -843,33 +1015,36 @@ __device__ void push_phase(const Args<T> &a, int r, T *red, Local<T> &L) {
     L.next_push.ctr = &a.ctrl->push_ctr[(r + 1) % 3];
     L.next_push.items = a.push_items[(r + 1) & 1];
     L.next_push.offs = a.push_offs[(r + 1) & 1];
-    if (lo >= total) return;
-    const int hi = min(total, lo + K);
-
-    int i = warp_find(offs, cnt, lo);
-    int x = lo;
-    while (x < hi) {
-        const int ii = i + lane;
-        const bool valid = ii < cnt;
-        int o = total, oend = total, beg = 0;
-        T val = T(0);
-        View vw = idle_view<MULTI>(a);
-        if (valid) {
-            const int g = ld_cg(items + ii) & 0x7fffffff;
-            vw = view_of<MULTI>(a, g);
-            const int v = g - vw.delta;
-            o = ld_cg(offs + ii);
-            oend = ii + 1 < cnt ? ld_cg(offs + ii + 1) : total;
-            beg = __ldg(A.rrow_ptr + v);
-            if (o >= lo && o < hi) atomicAnd(bits_cur + (g >> 5), ~(1u << (g & 31)));  // consumed
-            val = ld_cg(a.f + g);
+    const ChunkPlan cp = chunk_plan(total, a.chunk);
+    for (long long c = cp.first; c * cp.K < total; c = next_chunk(cp, &a.ctrl->push_take[r % 3])) {
+        const int lo = (int)(c * cp.K);
+        const int hi = (int)min((long long)total, c * cp.K + cp.K);
+        int i = warp_find(offs, cnt, lo);
+        int x = lo;
+        while (x < hi) {
+            const int ii = i + lane;
+            const bool valid = ii < cnt;
+            int o = total, oend = total, beg = 0;
+            T val = T(0);
+            View vw = idle_view<MULTI>(a);
+            if (valid) {
+                const int g = ld_cg(items + ii) & 0x7fffffff;
+                vw = view_of<MULTI>(a, g);
+                const int v = g - vw.delta;
+                o = ld_cg(offs + ii);
+                oend = ii + 1 < cnt ? ld_cg(offs + ii + 1) : total;
+                beg = __ldg(A.rrow_ptr + v);
+                if (o >= lo && o < hi) atomicAnd(bits_cur + (g >> 5), ~(1u << (g & 31)));  // consumed
+                val = ld_cg(a.f + g);
+            }
+            const int stop = min(hi, __shfl_sync(FULL, oend, 31));
+            push_edges<MULTI, T>(a, r, beg, o, val, vw, x, stop, L);
+            x = stop;
+            i += 32;
         }
-        const int stop = min(hi, __shfl_sync(FULL, oend, 31));
-        push_edges<MULTI, T>(a, r, beg, o, val, vw, x, stop, L);
-        x = stop;
-        i += 32;
+        // the local worklist after each chunk, while its vertices are near the sweep
+        drain_local<MULTI, T>(a, r, red, L);
     }
-    drain_local<MULTI, T>(a, r, red, L);
     stage_flush(L.next_pull);
     stage_flush(L.next_push);
 }
@@ -905,6 +1080,10 @@ __global__ void __launch_bounds__(THREADS, EG_FIXPOINT_MIN_BLOCKS) k_fixpoint(Ar
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             c->pull_ctr[(r + 2) % 3] = 0;
             c->push_ctr[(r + 2) % 3] = 0;
+            // round r + 1's take counters (round r's were cleared one round
+            // earlier, or by the launch's reset of the control block)
+            c->pull_take[(r + 1) % 3] = 0;
+            c->push_take[(r + 1) % 3] = 0;
         }
         const unsigned long long pc = ld_cg(&c->pull_ctr[r % 3]);
         if ((pc & 0xffffffffu) != 0) {
@@ -1174,6 +1353,8 @@ struct Launch {
     const int *level = nullptr;        // SCC-ordered solves: level of each vertex
     int cur_level = 0;                 //   and the level this launch solves (0 first)
     long long slice_rounds = 0;        // > 0: the launch stops after this many rounds, without error
+    int chunk_edges = 0;               // edges per chunk of a long list (0: one chunk per warp)
+    int sweeps = 0;                    // dense sweeps before the worklist rounds (not with levels)
 };
 
 // The arena's launch settings with the given warm start and round budget.
@@ -1181,6 +1362,8 @@ static Launch launch_of(const eg_arena *ar, int warm_start, long long max_rounds
     Launch L{ar->local_windows, ar->local_maxdeg, warm_start, ar->seed_max_pairs, max_rounds};
     L.blocks_per_sm = ar->blocks_per_sm;
     L.wait_ns = ar->wait_limit_ns;
+    L.chunk_edges = ar->chunk_edges;
+    L.sweeps = ar->sweeps;
     return L;
 }
 
@@ -1225,6 +1408,7 @@ static eg_status enqueue_solve(const DevArena &A, const WeightView &W, const Ins
     a.doorbell = nullptr;
     a.local_windows = L.local_windows;
     a.local_maxdeg = L.local_maxdeg;
+    a.chunk = L.chunk_edges;
     a.wait_ns = L.wait_ns;
     a.inv = L.inv;
     a.frozen = L.frozen;
@@ -1248,7 +1432,21 @@ static eg_status enqueue_solve(const DevArena &A, const WeightView &W, const Ins
             k_level_start<T><<<init_blocks, THREADS, 0, s>>>(a.f, (int)nf, a.seed_bits);
         k_init_level<T><<<init_blocks, THREADS, 0, s>>>(a, L.cur_level);
     } else {
-        k_init<MULTI, T><<<init_blocks, THREADS, 0, s>>>(a, 0, (int)nf, 0, 0);
+        k_init<MULTI, T><<<init_blocks, THREADS, 0, s>>>(a, 0, (int)nf, 0, 0, L.sweeps > 0 ? 0 : 1);
+        EG_CUDA_TRY(cudaGetLastError());
+        if (L.sweeps > 0) {
+            static int sweep_per_sm[64] = {0};  // resident sweep blocks per SM, per device
+            int sp = device >= 0 && device < 64 ? sweep_per_sm[device] : 0;
+            if (sp < 1) {
+                EG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sp, k_sweep<MULTI, T>, THREADS, 0));
+                sp = std::max(sp, 1);
+                if (device >= 0 && device < 64) sweep_per_sm[device] = sp;
+            }
+            // one resident wave: the grid moves through the credits together
+            const int sw_blocks = (int)std::min<long long>((nf + THREADS - 1) / THREADS, (long long)sms * sp);
+            for (int k = 0; k < L.sweeps; ++k)
+                k_sweep<MULTI, T><<<sw_blocks, THREADS, 0, s>>>(a, k == L.sweeps - 1 ? 1 : 0);
+        }
     }
     EG_CUDA_TRY(cudaGetLastError());
 
@@ -1891,6 +2089,7 @@ struct eg_plan_impl {
     std::vector<int> fbase, delta, n_of, bits_alone;
     std::vector<long long> scale, shift, C;
     void *table = nullptr;  // device instance table
+    int *lut = nullptr;     // device block lookup of the instance table (non-uniform instances)
     InstTable I{};
     StateBuffers sb;
     cudaStream_t own = nullptr;
@@ -1898,7 +2097,7 @@ struct eg_plan_impl {
     void *host_ctrl = nullptr;
     cudaGraphExec_t graph = nullptr;
     long long graph_rounds = -1;
-    int graph_opts[4] = {-1, -1, -1, -1};
+    int graph_opts[6] = {-1, -1, -1, -1, -1, -1};
     long long graph_pairs = -1;
     unsigned long long graph_wait = 0;
     bool graph_failed = false;
@@ -1922,6 +2121,7 @@ eg_status plan_release(eg_plan_impl *p) {
     free_state(p->sd);
     if (p->cert_block) cudaFree(p->cert_block);
     if (p->table) cudaFree(p->table);
+    if (p->lut) cudaFree(p->lut);
     if (p->own) cudaStreamDestroy(p->own);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
@@ -2021,6 +2221,27 @@ eg_status plan_create(eg_arena *ar, int count, const int32_t *part, const int64_
     for (int i = 1; i < count; ++i)
         if (p->n_of[i] != uniform) uniform = 0;
     p->I = InstTable{count, uniform, d_fbase, d_delta, d_scale, d_shift, d_C};
+    if (!uniform) {
+        // block lookup of the instance of a credit: blocks of 2^shift credits,
+        // no longer than the shortest instance, so at most one step past it
+        int min_n = p->n_of[0];
+        for (int i = 1; i < count; ++i) min_n = std::min(min_n, p->n_of[i]);
+        int shift = 0;
+        while (shift < 20 && (2 << shift) <= min_n) ++shift;
+        const size_t blocks = (size_t)(nf >> shift) + 1;
+        std::vector<int> lut(blocks);
+        int i = 0;
+        for (size_t b = 0; b < blocks; ++b) {
+            const long long x = (long long)b << shift;
+            while (i + 1 < count && p->fbase[i + 1] <= x) ++i;
+            lut[b] = i;
+        }
+        PTRY(cudaMalloc((void **)&p->lut, blocks * 4));
+        PTRY(cudaMemcpyAsync(p->lut, lut.data(), blocks * 4, cudaMemcpyHostToDevice, s));
+        PTRY(cudaStreamSynchronize(s));
+        p->I.lut = p->lut;
+        p->I.lut_shift = shift;
+    }
     const int sms = num_sms(ar->device);
     k_bound_inst<<<(int)std::min<long long>((nf + 255) / 256, (long long)sms * 32), 256, 0, s>>>(
         ar->d, p->I, (int)nf, d_accC, d_accW);
@@ -2306,7 +2527,9 @@ eg_status plan_run(eg_plan_impl *p, void *out, eg_stats *st, cudaStream_t user, 
     }
     const bool same = p->graph && p->graph_rounds == L.max_rounds && p->graph_opts[0] == L.local_windows &&
                       p->graph_opts[1] == L.local_maxdeg && p->graph_opts[2] == L.warm_start &&
-                      p->graph_opts[3] == L.blocks_per_sm && p->graph_pairs == L.seed_max_pairs &&
+                      p->graph_opts[3] == L.blocks_per_sm && p->graph_opts[4] == L.chunk_edges &&
+                      p->graph_opts[5] == L.sweeps &&
+                      p->graph_pairs == L.seed_max_pairs &&
                       p->graph_wait == L.wait_ns;
     if (!ar->use_graph && p->graph) {
         cudaGraphExecDestroy(p->graph);
@@ -2332,6 +2555,8 @@ eg_status plan_run(eg_plan_impl *p, void *out, eg_stats *st, cudaStream_t user, 
             p->graph_opts[1] = L.local_maxdeg;
             p->graph_opts[2] = L.warm_start;
             p->graph_opts[3] = L.blocks_per_sm;
+            p->graph_opts[4] = L.chunk_edges;
+            p->graph_opts[5] = L.sweeps;
             p->graph_pairs = L.seed_max_pairs;
             p->graph_wait = L.wait_ns;
         } else {
@@ -2518,6 +2743,7 @@ static Args<long long> resident_args(const Resident &R) {
     a.doorbell = R.bell_dev;
     a.local_windows = R.local_windows;
     a.local_maxdeg = R.local_maxdeg;
+    a.chunk = R.chunk_edges;
     a.wait_ns = BARRIER_LIMIT_NS;
     a.level = nullptr;
     a.cur_level = 0;
@@ -2609,7 +2835,7 @@ eg_status resident_admit(Resident &R, int slot, int g0, int n, long long scale, 
     a.seed_bits = R.sb.d.seed_bits;
     const int r = (int)R.r;
     const int iblocks = (int)std::min<long long>((n + THREADS - 1) / THREADS, (long long)sms * 16);
-    k_init<true, long long><<<iblocks, THREADS, 0, s>>>(a, g0, g0 + n, r % 3, r & 1);
+    k_init<true, long long><<<iblocks, THREADS, 0, s>>>(a, g0, g0 + n, r % 3, r & 1, 1);
     EG_CUDA_TRY(cudaGetLastError());
     return EG_OK;
 }

@@ -3,9 +3,10 @@
 //
 // The settings that change how fast the least fixpoint is reached -- never
 // the result -- are the per-warp local worklist budget and its degree
-// threshold, the resident blocks per SM of the persistent kernel, the first
-// trial cap of the certified route and the round budget of the first
-// attempt.  The best values depend on the arena: R-MAT's power-law rows
+// threshold, the resident blocks per SM of the persistent kernel, the dense
+// sweeps before the worklist rounds, the chunk size of long worklists, and
+// the certified route's first trial cap, dual K, cycle-jump slice length and
+// the round budget of its first attempt.  The best values depend on the arena: R-MAT's power-law rows
 // finish in a few rounds, a road-like grid climbs for thousands of rounds
 // through the certified trials.  The tuner times real solves (each one exact)
 // in a coordinate search from the arena's current settings and keeps a
@@ -53,25 +54,54 @@ __global__ void k_degree_hist(DevArena A, unsigned long long *hist) {
 }
 
 struct Settings {
-    int local_windows, local_maxdeg, blocks_per_sm, cap_certify;
-    long long certify_after;
-    int dual_k;
-    long long kick_rounds;
+    long long v[9];  // the values of the tuned options, in the order of DIMS
 };
 
+// The options the search tunes, with their candidate values.  `trials`:
+// the option only matters where the certified trials run.
+struct Dim {
+    const char *name;  // the field's name in the cache file
+    bool trials;
+    int nvals;
+    long long vals[6];
+};
+static const Dim DIMS[9] = {
+    {"local_windows", false, 6, {0, 16, 32, 64, 128, 256}},
+    {"local_maxdeg", false, 5, {8, 16, 32, 64, 256}},
+    {"blocks_per_sm", false, 4, {1, 2, 3, 0}},
+    {"cap_certify", true, 4, {2, 4, 8, 16}},
+    {"certify_after", true, 5, {0, 4, 8, 16, 32}},
+    {"dual_k", true, 4, {1, 2, 4, 8}},
+    {"kick_rounds", true, 5, {0, 1, 2, 4, 8}},
+    {"sweeps", false, 5, {0, 1, 2, 4, 8}},
+    {"chunk_edges", false, 5, {0, 512, 1024, 2048, 4096}},
+};
+enum { D_LW, D_MD, D_BPS, D_CC, D_CA, D_DK, D_KR, D_SW, D_CH };
+
 static Settings settings_of(const eg_arena *ar) {
-    return Settings{ar->local_windows, ar->local_maxdeg, ar->blocks_per_sm, ar->cap_certify, ar->certify_after,
-                    ar->dual_k, ar->kick_rounds};
+    Settings S;
+    S.v[D_LW] = ar->local_windows;
+    S.v[D_MD] = ar->local_maxdeg;
+    S.v[D_BPS] = ar->blocks_per_sm;
+    S.v[D_CC] = ar->cap_certify;
+    S.v[D_CA] = ar->certify_after;
+    S.v[D_DK] = ar->dual_k;
+    S.v[D_KR] = ar->kick_rounds;
+    S.v[D_SW] = ar->sweeps;
+    S.v[D_CH] = ar->chunk_edges;
+    return S;
 }
 
 static void apply(eg_arena *ar, const Settings &S) {
-    ar->local_windows = S.local_windows;
-    ar->local_maxdeg = S.local_maxdeg;
-    ar->blocks_per_sm = S.blocks_per_sm;
-    ar->cap_certify = S.cap_certify;
-    ar->certify_after = S.certify_after;
-    ar->dual_k = S.dual_k;
-    ar->kick_rounds = S.kick_rounds;
+    ar->local_windows = (int)S.v[D_LW];
+    ar->local_maxdeg = (int)S.v[D_MD];
+    ar->blocks_per_sm = (int)S.v[D_BPS];
+    ar->cap_certify = (int)S.v[D_CC];
+    ar->certify_after = S.v[D_CA];
+    ar->dual_k = (int)S.v[D_DK];
+    ar->kick_rounds = S.v[D_KR];
+    ar->sweeps = (int)S.v[D_SW];
+    ar->chunk_edges = (int)S.v[D_CH];
 }
 
 static int ilog2(double x) { return x <= 1.0 ? 0 : (int)std::lround(std::log2(x)); }
@@ -166,15 +196,15 @@ static bool cache_lookup(const char *path, const std::string &key, Settings &S, 
     for (const std::string &line : read_lines(path)) {
         std::string k;
         if (!key_of(line, k) || k != key) continue;
-        long long lw, md, bps, cc, ca, dk, kr, us = -1;
-        if (field(line, "local_windows", lw) && field(line, "local_maxdeg", md) && field(line, "blocks_per_sm", bps) &&
-            field(line, "cap_certify", cc) && field(line, "certify_after", ca) && field(line, "dual_k", dk) &&
-            field(line, "kick_rounds", kr)) {
-            field(line, "tuned_us", us);
-            S = Settings{(int)lw, (int)md, (int)bps, (int)cc, ca, (int)dk, kr};
-            ms = us >= 0 ? us * 1e-3 : -1.0;
-            return true;
-        }
+        Settings c;
+        bool all = true;
+        for (int d = 0; d < 9 && all; ++d) all = field(line, DIMS[d].name, c.v[d]);
+        if (!all) continue;  // a line of an older field set: not a hit
+        long long us = -1;
+        field(line, "tuned_us", us);
+        S = c;
+        ms = us >= 0 ? us * 1e-3 : -1.0;
+        return true;
     }
     return false;
 }
@@ -186,14 +216,10 @@ static eg_status cache_store(const char *path, const std::string &key, const Set
         if (key_of(line, k) && k == key) continue;
         keep.push_back(line);
     }
-    char buf[512];
-    snprintf(buf, sizeof(buf),
-             "{\"key\": \"%s\", \"local_windows\": %d, \"local_maxdeg\": %d, \"blocks_per_sm\": %d, "
-             "\"cap_certify\": %d, \"certify_after\": %lld, \"dual_k\": %d, \"kick_rounds\": %lld, "
-             "\"tuned_us\": %lld}",
-             key.c_str(), S.local_windows, S.local_maxdeg, S.blocks_per_sm, S.cap_certify, S.certify_after,
-             S.dual_k, S.kick_rounds, (long long)std::llround(ms * 1e3));
-    keep.push_back(buf);
+    std::string rec = "{\"key\": \"" + key + "\"";
+    for (int d = 0; d < 9; ++d) rec += std::string(", \"") + DIMS[d].name + "\": " + std::to_string(S.v[d]);
+    rec += ", \"tuned_us\": " + std::to_string((long long)std::llround(ms * 1e3)) + "}";
+    keep.push_back(rec);
     const std::string tmp = std::string(path) + ".tmp";
     FILE *fh = fopen(tmp.c_str(), "w");
     if (!fh) {
@@ -254,39 +280,17 @@ static eg_status search(eg_arena *ar, RunFn run, void *ctx, cudaStream_t s, int 
     solves = 1 + reps;
     best_ms = default_ms;
     Settings best = settings_of(ar);
-    const int lw[] = {0, 16, 32, 64, 128, 256};
-    const int md[] = {8, 16, 32, 64, 256};
-    const int bps[] = {1, 2, 3, 0};
-    const int cc[] = {2, 4, 8, 16};
-    const int dk[] = {1, 2, 4, 8};
-    const int ca[] = {0, 4, 8, 16, 32};
-    const int kr[] = {0, 1, 2, 4, 8};
-    // the route's settings first (the first attempt, the jumps' slices, the
-    // trials' cap and K): they change the work most
-    const int order[] = {4, 6, 3, 5, 0, 1, 2};
-    for (int dim : order) {
-        if ((dim == 3 || dim == 4 || dim == 5 || dim == 6) && !trials_matter) continue;
-        const int *vals = dim == 0   ? lw
-                          : dim == 1 ? md
-                          : dim == 2 ? bps
-                          : dim == 3 ? cc
-                          : dim == 5 ? dk
-                          : dim == 6 ? kr
-                                     : ca;
-        const int nv = dim == 0 ? 6 : (dim == 1 || dim == 4 || dim == 6) ? 5 : 4;
-        for (int k = 0; k < nv; ++k) {
+    // the settings that change the work most first: the first attempt's
+    // budget, the sweeps, the local worklist budget, then the trials' jump
+    // slices, cap and K
+    const int order[] = {D_CA, D_SW, D_LW, D_KR, D_CC, D_DK, D_CH, D_MD, D_BPS};
+    for (int d : order) {
+        if (DIMS[d].trials && !trials_matter) continue;
+        for (int k = 0; k < DIMS[d].nvals; ++k) {
             if (solves + reps > max_solves) break;
             Settings c = best;
-            int *slot = dim == 0 ? &c.local_windows : dim == 1 ? &c.local_maxdeg : dim == 2 ? &c.blocks_per_sm
-                                                      : dim == 5 ? &c.dual_k : &c.cap_certify;
-            if (dim == 4 || dim == 6) {
-                long long &v = dim == 4 ? c.certify_after : c.kick_rounds;
-                if (v == vals[k]) continue;
-                v = vals[k];
-            } else {
-                if (*slot == vals[k]) continue;
-                *slot = vals[k];
-            }
+            if (c.v[d] == DIMS[d].vals[k]) continue;
+            c.v[d] = DIMS[d].vals[k];
             apply(ar, c);
             double ms = 0;
             rc = timed(run, ctx, s, reps, ms);
@@ -329,13 +333,15 @@ static eg_status run_plan(void *p, cudaStream_t s) {
 
 static void fill(eg_tuning *out, const Settings &S, double d, double t, int solves, int cached, const std::string &key) {
     if (!out) return;
-    out->local_windows = S.local_windows;
-    out->local_maxdeg = S.local_maxdeg;
-    out->blocks_per_sm = S.blocks_per_sm;
-    out->cap_certify = S.cap_certify;
-    out->certify_after = S.certify_after;
-    out->dual_k = S.dual_k;
-    out->kick_rounds = (int32_t)S.kick_rounds;
+    out->local_windows = (int32_t)S.v[D_LW];
+    out->local_maxdeg = (int32_t)S.v[D_MD];
+    out->blocks_per_sm = (int32_t)S.v[D_BPS];
+    out->cap_certify = (int32_t)S.v[D_CC];
+    out->certify_after = S.v[D_CA];
+    out->dual_k = (int32_t)S.v[D_DK];
+    out->kick_rounds = (int32_t)S.v[D_KR];
+    out->sweeps = (int32_t)S.v[D_SW];
+    out->chunk_edges = (int32_t)S.v[D_CH];
     out->default_ms = d;
     out->tuned_ms = t;
     out->solves = solves;

@@ -84,6 +84,7 @@ class eg_tuning(ctypes.Structure):
     _fields_ = [("local_windows", ctypes.c_int32), ("local_maxdeg", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("cap_certify", ctypes.c_int32),
                 ("certify_after", ctypes.c_int64), ("dual_k", ctypes.c_int32), ("kick_rounds", ctypes.c_int32),
+                ("sweeps", ctypes.c_int32), ("chunk_edges", ctypes.c_int32),
                 ("default_ms", ctypes.c_double), ("tuned_ms", ctypes.c_double),
                 ("solves", ctypes.c_int32), ("from_cache", ctypes.c_int32), ("key", ctypes.c_char * 96)]
 
@@ -210,6 +211,8 @@ EG_OPT_WAIT_LIMIT_US = 9
 EG_OPT_SCC_ORDER = 10
 EG_OPT_DUAL_K = 11
 EG_OPT_KICK_ROUNDS = 12
+EG_OPT_CHUNK_EDGES = 13
+EG_OPT_SWEEPS = 14
 
 
 def eg_solve_credit_noalloc(arena, credit_bits, w_scale, w_shift, credits_out, stream=None, max_rounds=0,
@@ -286,13 +289,14 @@ class Arena:
 
     def tune(self, local_windows=None, local_maxdeg=None, warm_start=None, seed_max_pairs=None, cap_certify=None,
              certify_after=None, blocks_per_sm=None, wait_limit_us=None, scc_order=None, dual_k=None,
-             kick_rounds=None):
+             kick_rounds=None, chunk_edges=None, sweeps=None):
         for opt, val in ((EG_OPT_LOCAL_WINDOWS, local_windows), (EG_OPT_LOCAL_MAXDEG, local_maxdeg),
                          (EG_OPT_WARM_START, warm_start), (EG_OPT_SEED_MAX_PAIRS, seed_max_pairs),
                          (EG_OPT_CAP_CERTIFY, cap_certify), (EG_OPT_CERTIFY_AFTER, certify_after),
                          (EG_OPT_BLOCKS_PER_SM, blocks_per_sm), (EG_OPT_WAIT_LIMIT_US, wait_limit_us),
                          (EG_OPT_SCC_ORDER, scc_order), (EG_OPT_DUAL_K, dual_k),
-                         (EG_OPT_KICK_ROUNDS, kick_rounds)):
+                         (EG_OPT_KICK_ROUNDS, kick_rounds), (EG_OPT_CHUNK_EDGES, chunk_edges),
+                         (EG_OPT_SWEEPS, sweeps)):
             if val is not None:
                 eg_set_option(self.handle, opt, int(val))
 
