@@ -59,12 +59,12 @@ def algorithmic_bytes(st, s):
     return st["relaxations"] * (8 + s) + (st["lifts"] + st["pushes"]) * (12 + s) + st["enqueues"] * 8
 
 
-def launches_of(st):
-    """Kernels of one single-game solve: warm start, init and the fixpoint per
-    fixpoint launch, plus the trials' bitmap passes (3 after a capped lift,
-    2 after a dual lift)."""
+def launches_of(st, sweeps=0):
+    """Kernels of one single-game solve: warm start, init, `sweeps` dense
+    sweeps and the fixpoint per fixpoint launch, plus the trials' bitmap
+    passes (3 after a capped lift, 2 after a dual lift)."""
     kinds = [p["kind"] for p in st["phase_list"]]
-    return 3 * len(kinds) + 3 * kinds.count("capped") + 2 * kinds.count("dual")
+    return (3 + sweeps) * len(kinds) + 3 * kinds.count("capped") + 2 * kinds.count("dual")
 
 
 def strip_comments(src):
@@ -314,7 +314,7 @@ def rmat_context(eg, gen, torch, dev, stream, flush, plain_start=True, tune=True
                           "traffic": traffic_record("fixpoint_rmat20_traffic.json",
                                                     {k: tuning[k] for k in SETTING_KEYS} if tuning
                                                     else dict(DEFAULT_SETTINGS)),
-                          "kernel": "k_fixpoint"},
+                          "kernel": "k_sweep + k_fixpoint (the lifting kernels)"},
              "oracle": None, "settings": "autotuned (eg_autotune)" if tuning else "defaults", "tuning": tuning}
     if g:
         out_d["oracle"] = {"time_to_fixpoint_s": g["oracle_seconds"], "route": "Algorithm 1 with cap C, 1 thread",
@@ -553,6 +553,9 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched threshold-query comparison")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement")
     ap.add_argument("--no-tune", action="store_true", help="time the default settings (no eg_autotune)")
+    ap.add_argument("--settings", default=None,
+                    help="headline launch settings as JSON ({\"local_windows\": 32, ...}), applied instead of "
+                         "eg_autotune (e.g. to profile the tuned route without its search)")
     ap.add_argument("--no-scc", action="store_true", help="skip the SCC-ordered context solves")
     ap.add_argument("--batch-games", type=int, default=4096, help="games in the batched-vs-per-game comparison "
                     "(4096 = the full workload; 0 skips it)")
@@ -596,7 +599,13 @@ def main():
     # launch settings picked by the library's autotuner (timed solves, each
     # exact), outside the timed region; a fresh cache file, so it searches
     tuning = None
-    if not args.no_tune:
+    given = json.loads(args.settings) if args.settings else None
+    if given:
+        unknown = set(given) - set(SETTING_KEYS)
+        if unknown:
+            raise SystemExit(f"--settings: unknown keys {sorted(unknown)}")
+        arena.tune(**given)
+    elif not args.no_tune:
         import tempfile
 
         t0 = time.perf_counter()
@@ -628,22 +637,22 @@ def main():
     step_ms = [b.elapsed_time(e) for b, e in ev]
     total_ms = sum(step_ms)
     relax = sum(x["relaxations"] for x in stats)
-    launches = sum(launches_of(x) for x in stats)
+    settings = {k: tuning[k] for k in SETTING_KEYS} if tuning else dict(DEFAULT_SETTINGS, **(given or {}))
+    launches = sum(launches_of(x, settings["sweeps"]) for x in stats)
     if pg:
         total_ms_max, relax_all = reduce_over_ranks(total_ms, relax, dev, pg)
     else:
         total_ms_max, relax_all = total_ms, float(relax)
     ok = all(x["status"] == 0 for x in stats)
 
-    # dominant kernel: the persistent fixpoint; the library times every launch
-    # of it with CUDA events on the solve's stream (phase_ms), summed here over
-    # all launches of all timed steps
+    # dominant kernels: the lifting (dense sweeps and the persistent fixpoint);
+    # the library times every lifting launch with CUDA events on the solve's
+    # stream (phase_ms), summed here over all launches of all timed steps
     fix_ms = sum(x["fixpoint_ms"] for x in stats)
     n_launch = sum(x["phases"] for x in stats)
     bytes_alg = sum(algorithmic_bytes(x, s) for x in stats)
     peak, peak_kind = peaks()
     achieved = bytes_alg / (fix_ms * 1e-3) / 1e9
-    settings = {k: tuning[k] for k in SETTING_KEYS} if tuning else dict(DEFAULT_SETTINGS)
     traffic = traffic_record(f"fixpoint_grid{side}_traffic.json", settings)
 
     # end to end through the public API: the arena from pinned host arrays
@@ -756,7 +765,7 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed between steps (512 MiB write); arena and state exceed L2"},
         "all_exact": ok,
-        "settings": "autotuned (eg_autotune)" if tuning else "defaults",
+        "settings": "autotuned (eg_autotune)" if tuning else "given (--settings)" if given else "defaults",
         "launch_settings": settings,
         "tuning": tuning,
         "time_to_fixpoint_ms": statistics.median(step_ms),
@@ -764,9 +773,10 @@ def main():
         "rounds": st0["rounds"], "relaxations_per_step": st0["relaxations"], "lifts": st0["lifts"],
         "pushes": st0["pushes"], "trials": st0["trials"], "phases": st0["phase_list"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": traffic, "kernel": "k_fixpoint", "peak_kind": peak_kind,
-                     "per": "step: every k_fixpoint launch of one solve (the attempt and each slice of the "
-                            "trials' lifts)",
+                     "traffic": traffic, "kernel": "k_sweep + k_fixpoint (the lifting kernels)",
+                     "peak_kind": peak_kind,
+                     "per": "step: every lifting launch of one solve (the dense sweeps and the fixpoint kernel of "
+                            "the attempt and of each slice of the trials' lifts)",
                      "phases_per_step": n_launch / args.steps,
                      "algorithmic_bytes_per_step": bytes_alg / args.steps,
                      "kernel_ms_per_step": fix_ms / args.steps},

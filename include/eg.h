@@ -77,7 +77,8 @@ typedef struct eg_stats {
     int64_t relaxations;
     int64_t enqueues;
     double ms;             /* device time of initialisation + fixpoint kernels */
-    double fixpoint_ms;    /* device time of the persistent fixpoint kernel alone */
+    double fixpoint_ms;    /* device time of the lifting kernels alone: the dense sweeps
+                            * (EG_OPT_SWEEPS) and the persistent fixpoint kernel */
     int64_t cycle_jumps;   /* vertices raised by cycle jumps (EG_OPT_KICK_ROUNDS) */
     /* The fixpoint launches of the solve in order, the first EG_MAX_PHASES
      * of them: a single solve runs a first attempt with cap C and, when that
@@ -89,7 +90,7 @@ typedef struct eg_stats {
     int64_t phase_cap[EG_MAX_PHASES];         /* the launch's cap: C, (K + 1) B or B */
     int64_t phase_rounds[EG_MAX_PHASES];
     int64_t phase_relaxations[EG_MAX_PHASES];
-    double phase_ms[EG_MAX_PHASES];           /* device time of its fixpoint kernel */
+    double phase_ms[EG_MAX_PHASES];           /* device time of its sweeps and fixpoint kernel */
 } eg_stats;
 
 /*

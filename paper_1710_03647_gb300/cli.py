@@ -61,7 +61,7 @@ def main(argv=None) -> None:
 
 
 def batch(args) -> None:
-    games = [gen.batch_game(i, n, W, seed=args.seed) for i, (n, W) in enumerate(gen.batch_shapes(args.games))]
+    games = gen.batch_games(args.games, seed=args.seed)
     n, row_ptr, col, w, owner_bits, part_ptr = eg.pack_games(games)
     with eg.Arena(gen.Arena(n, row_ptr, col, w, owner_bits, "batch")) as arena:
         arena.tune(local_windows=args.local_windows, local_maxdeg=args.local_maxdeg, warm_start=args.warm_start,

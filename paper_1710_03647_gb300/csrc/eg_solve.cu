@@ -1367,8 +1367,9 @@ static Launch launch_of(const eg_arena *ar, int warm_start, long long max_rounds
     return L;
 }
 
-// Enqueues (warm start,) initialisation and the persistent fixpoint on
-// stream s; ev_k (optional) is recorded right before the fixpoint kernel.
+// Enqueues (warm start,) initialisation, the dense sweeps and the persistent
+// fixpoint on stream s; ev_k (optional) is recorded right before the lifting
+// kernels (the sweeps, or the fixpoint kernel when there are none).
 template <bool MULTI, typename T>
 static eg_status enqueue_solve(const DevArena &A, const WeightView &W, const InstTable &I, long long nf,
                                StateBuffers &sb, const Launch &L, int device, cudaStream_t s, cudaEvent_t ev_k,
@@ -1434,6 +1435,7 @@ static eg_status enqueue_solve(const DevArena &A, const WeightView &W, const Ins
     } else {
         k_init<MULTI, T><<<init_blocks, THREADS, 0, s>>>(a, 0, (int)nf, 0, 0, L.sweeps > 0 ? 0 : 1);
         EG_CUDA_TRY(cudaGetLastError());
+        if (ev_k && L.sweeps > 0) EG_CUDA_TRY(cudaEventRecord(ev_k, s));  // the lifting starts with the sweeps
         if (L.sweeps > 0) {
             static int sweep_per_sm[64] = {0};  // resident sweep blocks per SM, per device
             int sp = device >= 0 && device < 64 ? sweep_per_sm[device] : 0;
@@ -1463,7 +1465,7 @@ static eg_status enqueue_solve(const DevArena &A, const WeightView &W, const Ins
     if (L.blocks_per_sm > 0) per_sm = std::min(per_sm, L.blocks_per_sm);
     dim3 grid(sms * per_sm), block(THREADS);
     void *args[] = {&a};
-    if (ev_k) EG_CUDA_TRY(cudaEventRecord(ev_k, s));
+    if (ev_k && (L.sweeps == 0 || L.level)) EG_CUDA_TRY(cudaEventRecord(ev_k, s));
     EG_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_fixpoint<MULTI, T>, grid, block, args, 0, s));
     if (keep) *keep = a;  // for the launches that resume it
     if (grid_blocks) *grid_blocks = (int)grid.x;
