@@ -59,6 +59,38 @@ def algorithmic_bytes(st, s):
     return st["relaxations"] * (8 + s) + (st["lifts"] + st["pushes"]) * (12 + s) + st["enqueues"] * 8
 
 
+INT32_ROOM = 2**31 - 2  # largest cap + |weight| an int32 credit array holds below its TOP
+
+
+def lift_widths(st, wmax):
+    """Credit width (bits) of each lifting launch of a single-game solve, by
+    the library's rule: a trial lift (capped, or the dual with weights
+    -(K w' + 1)) whose cap plus largest |weight| fits int32 computes in
+    int32; the other launches at the solve's width.  K of a dual is its cap
+    over the preceding capped lift's cap, minus one."""
+    out, B = [], None
+    for p in st["phase_list"]:
+        if p["kind"] == "capped":
+            B = p["cap"]
+            out.append(32 if B + wmax <= INT32_ROOM else st["credit_bits"])
+        elif p["kind"] == "dual" and B:
+            K = p["cap"] // B - 1
+            out.append(32 if p["cap"] + K * wmax + 1 <= INT32_ROOM else 64)
+        else:
+            out.append(st["credit_bits"])
+    return out
+
+
+def credit_bytes(st, wmax):
+    """Bytes per credit of a solve's lifting, its launches weighted by their
+    relaxations (the trial lifts may compute narrower than the solve)."""
+    w = lift_widths(st, wmax)
+    rel = [p["relaxations"] for p in st["phase_list"]]
+    if not w or sum(rel) == 0:
+        return st["credit_bits"] / 8
+    return sum(r * b for r, b in zip(rel, w)) / sum(rel) / 8
+
+
 def launches_of(st, sweeps=0):
     """Kernels of one single-game solve: warm start, init, `sweeps` dense
     sweeps and the fixpoint per fixpoint launch, plus the trials' bitmap
@@ -303,7 +335,8 @@ def rmat_context(eg, gen, torch, dev, stream, flush, plain_start=True, tune=True
     ms = statistics.median(r[0] for r in res)
     relax = sum(r[1]["relaxations"] for r in res)
     fix_ms = sum(r[1]["fixpoint_ms"] for r in res)
-    bytes_alg = sum(algorithmic_bytes(r[1], s) for r in res)
+    wmax = int(np.abs(np.asarray(a.w, dtype=np.int64)).max())
+    bytes_alg = sum(algorithmic_bytes(r[1], credit_bytes(r[1], wmax)) for r in res)
     peak, peak_kind = peaks()
     g = golden(CONTEXT_RMAT["golden"])
     out_d = {"workload": CONTEXT_RMAT["workload"], "n": a.n, "m": a.m, "credit_bits": bits,
@@ -650,7 +683,8 @@ def main():
     # stream (phase_ms), summed here over all launches of all timed steps
     fix_ms = sum(x["fixpoint_ms"] for x in stats)
     n_launch = sum(x["phases"] for x in stats)
-    bytes_alg = sum(algorithmic_bytes(x, s) for x in stats)
+    wmax = int(np.abs(np.asarray(a.w, dtype=np.int64)).max())
+    bytes_alg = sum(algorithmic_bytes(x, credit_bytes(x, wmax)) for x in stats)
     peak, peak_kind = peaks()
     achieved = bytes_alg / (fix_ms * 1e-3) / 1e9
     traffic = traffic_record(f"fixpoint_grid{side}_traffic.json", settings)

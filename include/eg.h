@@ -212,6 +212,8 @@ eg_status eg_strategy(eg_arena *arena, int32_t credit_bits, int64_t w_scale, int
  *     TOP starts.
  *     This turns the pseudo-polynomial climb of player-1 vertices to C into
  *     climbs to B.  0 turns it off.  max_rounds bounds each fixpoint launch.
+ *     A trial lift whose cap plus max|w| fits int32 computes in int32
+ *     whatever the solve's width (not in eg_solve_credit_noalloc).
  *   EG_OPT_CERTIFY_AFTER (default 8): with certification on, a plain solve
  *     (cap C, warm start) runs first with this round budget, and the trials
  *     start only if it does not reach the fixpoint; 0 starts with the trials.

@@ -309,6 +309,7 @@ static eg_status destroy(eg_arena *a) {
     free_state(a->st32);
     free_state(a->st64);
     free_state(a->st_dual);
+    free_state(a->st_dual32);
     if (a->scc_level) cudaFree(a->scc_level);
     if (a->scc_comp) cudaFree(a->scc_comp);
     if (a->block) cudaFree(a->block);

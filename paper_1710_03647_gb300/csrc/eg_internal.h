@@ -97,6 +97,7 @@ struct eg_arena {
     long long C_plain = -1, wmax_plain = -1;  // bound and max |w| for scale 1, shift 0
     eg::StateBuffers st32, st64;
     eg::StateBuffers st_dual;  // int64 state of the certified trials' dual lifts
+    eg::StateBuffers st_dual32;  // int32 state of the dual lifts whose cap and weights fit int32
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evk = nullptr;
     void *host_ctrl = nullptr;  // pinned copy of Ctrl
     int local_windows = 64;     // per-warp local worklist budget per round (0 disables chaining)

@@ -1826,10 +1826,16 @@ static eg_status certify(eg_arena *ar, SolveMem &m, long long scale, long long s
     const int wblocks = (int)std::min<long long>((n + 255) / 256, (long long)sms * 16);
     const InstTable all{};
     unsigned long long *h = (unsigned long long *)ar->host_ctrl;
-    // h[0] = credits of sb at TOP without a proof of loss, h[1] = proven losses
-    auto count = [&]() -> eg_status {
+    // A lift whose cap and weights fit int32 runs in int32 state: half the
+    // bytes per credit (a 16M-vertex credit array then fits in L2).  Not in
+    // the allocation-free array, which has one layout.
+    auto fits32 = [](long long cap, long long wm) { return cap + wm <= 0x7fffffffLL - 1; };
+    // h[0] = credits of the capped fixpoint (f, of width w) at TOP without a
+    // proof of loss, h[1] = proven losses
+    auto count = [&](const void *f, int w) -> eg_status {
         EG_CUDA_TRY(cudaMemsetAsync(m.aux, 0, 2 * sizeof(unsigned long long), s));
-        k_count_undecided<T><<<wblocks, 256, 0, s>>>((const T *)sb.d.f, m.cert_w1, (int)n, m.aux);
+        if (w == 32) k_count_undecided<int><<<wblocks, 256, 0, s>>>((const int *)f, m.cert_w1, (int)n, m.aux);
+        else k_count_undecided<long long><<<wblocks, 256, 0, s>>>((const long long *)f, m.cert_w1, (int)n, m.aux);
         EG_CUDA_TRY(cudaGetLastError());
         EG_CUDA_TRY(cudaMemcpyAsync(h, m.aux, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         EG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1841,39 +1847,55 @@ static eg_status certify(eg_arena *ar, SolveMem &m, long long scale, long long s
         if (K > LIM / inner || B > LIM / (K + 1)) break;
         t.trials = k + 1;
         // the game with cap B: proven player-1 vertices start at TOP
-        EG_CUDA_TRY(cudaMemcpyAsync(sb.d.seed_bits, m.cert_w1, words * 4, cudaMemcpyDeviceToDevice, s));
+        const bool narrow = sizeof(T) == 8 && !m.fixed && fits32(B, wmax);
+        if (narrow && (rc = ensure_state(ar, 32)) != EG_OK) return rc;
+        StateBuffers &sc = narrow ? ar->st32 : sb;  // the capped lift's state
+        const int cw = narrow ? 32 : (int)sizeof(T) * 8;
+        EG_CUDA_TRY(cudaMemcpyAsync(sc.d.seed_bits, m.cert_w1, words * 4, cudaMemcpyDeviceToDevice, s));
         Launch Lp = launch_of(ar, 1, max_rounds);
         Lp.preseeded = true;
-        rc = run_phase<T>(ar, m, sb, WeightView{scale, shift, B}, Lp, s, t, EG_PHASE_CAPPED, dev);
+        rc = narrow ? run_phase<int>(ar, m, sc, WeightView{scale, shift, B}, Lp, s, t, EG_PHASE_CAPPED, dev)
+                    : run_phase<T>(ar, m, sc, WeightView{scale, shift, B}, Lp, s, t, EG_PHASE_CAPPED, dev);
         if (rc != EG_OK || dev != DEV_OK) return rc;
         seeded = true;
         // the warm start's own finds are proven losses too
-        k_or_bits<<<(int)std::min<size_t>((words + 255) / 256, 1024), 256, 0, s>>>(m.cert_w1, sb.d.seed_bits,
+        k_or_bits<<<(int)std::min<size_t>((words + 255) / 256, 1024), 256, 0, s>>>(m.cert_w1, sc.d.seed_bits,
                                                                                    (int)words);
-        k_mark_finite<T><<<wblocks, 256, 0, s>>>((const T *)sb.d.f, (int)n, m.cert_w0, all);
+        if (cw == 32) k_mark_finite<int><<<wblocks, 256, 0, s>>>((const int *)sc.d.f, (int)n, m.cert_w0, all);
+        else k_mark_finite<long long><<<wblocks, 256, 0, s>>>((const long long *)sc.d.f, (int)n, m.cert_w0, all);
         EG_CUDA_TRY(cudaGetLastError());
-        if ((rc = count()) != EG_OK) return rc;
-        if (h[0] == 0) {
+        // an exact capped fixpoint computed in int32 goes to the solve's own
+        // state, where the output and an in-place caller find it
+        auto finish = [&]() -> eg_status {
             exact = true;
+            if (narrow) {
+                k_widen<<<(int)std::min<long long>((n + 255) / 256, 4096), 256, 0, s>>>(
+                    (const int *)sc.d.f, (long long *)sb.d.f, (int)n);
+                EG_CUDA_TRY(cudaGetLastError());
+            }
             return EG_OK;
-        }
+        };
+        if ((rc = count(sc.d.f, cw)) != EG_OK) return rc;
+        if (h[0] == 0) return finish();
         // the dual: proven player-0 vertices start at TOP, proven player-1
         // vertices are held at 0
-        EG_CUDA_TRY(cudaMemcpyAsync(sd.d.seed_bits, m.cert_w0, words * 4, cudaMemcpyDeviceToDevice, s));
+        const bool narrow_d = !m.fixed && fits32((K + 1) * B, K * wmax + 1);
+        if (narrow_d && (rc = alloc_state(ar->st_dual32, ar->n, 32)) != EG_OK) return rc;
+        StateBuffers &sdd = narrow_d ? ar->st_dual32 : sd;
+        EG_CUDA_TRY(cudaMemcpyAsync(sdd.d.seed_bits, m.cert_w0, words * 4, cudaMemcpyDeviceToDevice, s));
         Launch Ld = launch_of(ar, 1, max_rounds);
         Ld.inv = 1;
         Ld.preseeded = true;
         Ld.frozen = m.cert_w1;
         const WeightView Wd{-K * scale, 1 - K * shift, (K + 1) * B};
-        rc = run_phase<long long>(ar, m, sd, Wd, Ld, s, t, EG_PHASE_DUAL, dev);
+        rc = narrow_d ? run_phase<int>(ar, m, sdd, Wd, Ld, s, t, EG_PHASE_DUAL, dev)
+                      : run_phase<long long>(ar, m, sdd, Wd, Ld, s, t, EG_PHASE_DUAL, dev);
         if (rc != EG_OK || dev != DEV_OK) return rc;
-        k_mark_finite<long long><<<wblocks, 256, 0, s>>>((const long long *)sd.d.f, (int)n, m.cert_w1, all);
+        if (narrow_d) k_mark_finite<int><<<wblocks, 256, 0, s>>>((const int *)sdd.d.f, (int)n, m.cert_w1, all);
+        else k_mark_finite<long long><<<wblocks, 256, 0, s>>>((const long long *)sdd.d.f, (int)n, m.cert_w1, all);
         EG_CUDA_TRY(cudaGetLastError());
-        if ((rc = count()) != EG_OK) return rc;
-        if (h[0] == 0) {
-            exact = true;
-            return EG_OK;
-        }
+        if ((rc = count(sc.d.f, cw)) != EG_OK) return rc;
+        if (h[0] == 0) return finish();
         if (B > LIM / 4) break;
         B *= 4;
         K = std::min(K * 8, n + 1);
