@@ -449,8 +449,9 @@ def batch_games(eg, gen, torch, dev, stream, count, tune=True):
             "per_game_total_ms": total, "per_game_games_per_s": count / (total * 1e-3),
             "per_game_p50_ms": lat[len(lat) // 2], "per_game_p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
             "batched_equals_per_game": bool(same), "plan_tuning": tuning, "condensation": scc,
-            "note": "batched: one plan (one persistent launch, CUDA graph replay) over a packed arena; latency of "
-                    "every game in the batch = the batch time"}
+            "note": "batched: one plan (one persistent launch, CUDA graph replay) over a packed arena, tuned by "
+                    "eg_plan_autotune; latency of every game in the batch = the batch time; per game: one "
+                    "eg_solve_credit per resident arena with the library defaults"}
 
 
 def _rmat_game(args):
@@ -706,6 +707,8 @@ def main():
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             h = eg.eg_create(a.n, a.m, rp_h, col_h, w_h, owner_bits=ob_h)
+            for key, val in settings.items():  # the settings the timed steps ran with
+                eg.eg_set_option(h, getattr(eg, "EG_OPT_" + key.upper()), int(val))
             t1 = time.perf_counter()
             _, st = eg.eg_solve_credit(h, bits, 1, 0, host_out)
             eg.eg_destroy(h)
@@ -716,7 +719,8 @@ def main():
         e2e = {"value": e_relax / sum(e_times), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(host_out.numel() * host_out.element_size() + 128),
                "ms_per_step": 1e3 * sum(e_times) / len(e_times),
-               "eg_create_ms": 1e3 * statistics.median(e_create), "host_buffers": "pinned"}
+               "eg_create_ms": 1e3 * statistics.median(e_create), "host_buffers": "pinned",
+               "settings": "the timed steps' launch settings, set with eg_set_option on each new arena"}
 
     single = world == 1
     context = None
