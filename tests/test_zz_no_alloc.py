@@ -126,3 +126,24 @@ def test_noalloc_refuses_misaligned_output():
         with pytest.raises(eg.EGError) as ei:  # 4 bytes off an 8-byte boundary
             eg.eg_solve_credit_noalloc(ar.handle, 64, 1, 0, buf.data_ptr() + 4)
         assert ei.value.status == eg.EG_ERR_INVALID and "aligned" in str(ei.value)
+
+
+@pytest.mark.parametrize("sweeps,chunk", [(2, 32), (1, 1024)])
+def test_noalloc_with_sweeps_and_chunks(sweeps, chunk):
+    # the dense sweeps and chunked lists run in the allocation-free array too
+    # (the sweeps use only the credits and round 0's push list); the credits
+    # equal the allocating solve's and, on the grid, the oracle's
+    for make, bits in ((lambda: gen.grid_game(96, 128, seed=6), 64), (lambda: gen.rmat_game(13, 8, seed=7), 32)):
+        a = make()
+        dt = torch.int32 if bits == 32 else torch.int64
+        with eg.Arena(a) as ar:
+            ar.tune(sweeps=sweeps, chunk_edges=chunk, certify_after=0)
+            want = torch.empty(a.n, dtype=dt, device="cuda:0")
+            eg.eg_solve_credit(ar.handle, bits, 1, 0, want)
+            got = torch.full((a.n,), -7, dtype=dt, device="cuda:0")
+            rc, st = eg.eg_solve_credit_noalloc(ar.handle, bits, 1, 0, got, max_rounds=200000)
+            torch.cuda.synchronize()
+            assert rc == eg.EG_OK and st.status == eg.EG_OK
+            np.testing.assert_array_equal(got.cpu().numpy(), want.cpu().numpy())
+            if bits == 64:
+                np.testing.assert_array_equal(want.cpu().numpy(), _certified_oracle(a))
