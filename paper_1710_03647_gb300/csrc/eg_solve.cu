@@ -122,6 +122,8 @@ struct Args {
     unsigned long long wait_ns;  // limit of each grid-barrier wait
     const int *level;  // SCC-ordered solves: topological level of each vertex (or null)
     int cur_level;     // the level being solved; predecessors above it are left for later
+    const int *tiles;  // non-null: the 32-credit tiles (index g >> 5) the O(n) passes visit, ascending
+    long long ntiles;  //   and how many (the tiles covering the instances a batched lift works on)
 };
 
 // One instance's view of the arena, carried per list entry.  A negative C
@@ -210,6 +212,19 @@ __global__ void k_fill(T *p, long long n, T v) {
 }
 
 // ---------------------------------------------------------------------------
+// Tiles of an O(n) pass (warm start, init, sweeps, proofs, counts): warps
+// take 32-credit tiles in order.  A batched lift of the certified trials
+// works on few instances; its launches carry the ascending list of the tiles
+// that cover those instances, and the passes visit only these.  Lanes of
+// other instances in a boundary tile are skipped as everywhere else.
+__device__ __forceinline__ long long tile_count(const int *tiles, long long ntiles, int g0, int g1) {
+    return tiles ? ntiles : ((long long)(g1 - g0) + 31) / 32;
+}
+__device__ __forceinline__ int tile_base(const int *tiles, long long t, int g0) {
+    return tiles ? (__ldg(tiles + t) << 5) : g0 + (int)(t << 5);
+}
+
+// ---------------------------------------------------------------------------
 // Warm start.  A player-1 vertex u on a cycle of player-1 vertices whose
 // weight (under the weight view) is negative is won by player 1: player 1
 // can keep the play on that cycle forever, so every credit runs out
@@ -231,8 +246,9 @@ __global__ void k_seed(Args<T> a, long long max_pairs, unsigned *seed_bits, unsi
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     unsigned found_total = 0;
-    for (int base = g0 + gw * 32; base < g1; base += nw * 32) {
-        const int g = base + lane;
+    const long long ntiles = tile_count(a.tiles, a.ntiles, g0, g1);
+    for (long long t = gw; t < ntiles; t += nw) {
+        const int g = tile_base(a.tiles, t, g0) + lane;
         bool mine = false;  // a player-1 credit of this lane, within max_pairs
         View vw = idle_view<MULTI>(a);
         int u = 0, ob = 0, oe = 0, ib = 0, ie = 0;
@@ -343,9 +359,11 @@ __global__ void k_seed(Args<T> a, long long max_pairs, unsigned *seed_bits, unsi
 template <bool MULTI, typename T>
 __global__ void __launch_bounds__(THREADS) k_init(Args<T> a, int g0, int g1, int slot, int buf, int list) {
     const DevArena &A = a.A;
-    const int nthreads = gridDim.x * blockDim.x;
-    for (int base = g0 + blockIdx.x * blockDim.x; base < g1; base += nthreads) {
-        const int g = base + threadIdx.x;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const long long ntiles = tile_count(a.tiles, a.ntiles, g0, g1);
+    for (long long t = gw; t < ntiles; t += nw) {
+        const int g = tile_base(a.tiles, t, g0) + lane_id();
         bool want = false;
         int work = 0;
         if (g < g1 && in_active<MULTI>(a, g)) {
@@ -588,8 +606,9 @@ __global__ void __launch_bounds__(THREADS) k_sweep(Args<T> a, int last) {
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     unsigned long long relax = 0, lifts = 0;
-    for (int base = gw * 32; base < a.nf; base += nw * 32) {
-        const int g = base + lane;
+    const long long ntiles = tile_count(a.tiles, a.ntiles, 0, a.nf);
+    for (long long t = gw; t < ntiles; t += nw) {
+        const int g = tile_base(a.tiles, t, 0) + lane;
         bool on = g < a.nf && in_active<MULTI>(a, g);
         View vw = idle_view<MULTI>(a);
         bool p1 = false;
@@ -1355,6 +1374,8 @@ struct Launch {
     long long slice_rounds = 0;        // > 0: the launch stops after this many rounds, without error
     int chunk_edges = 0;               // edges per chunk of a long list (0: one chunk per warp)
     int sweeps = 0;                    // dense sweeps before the worklist rounds (not with levels)
+    const int *tiles = nullptr;        // non-null: the tiles the O(n) passes visit (see Args)
+    long long ntiles = 0;
 };
 
 // The arena's launch settings with the given warm start and round budget.
@@ -1415,6 +1436,8 @@ static eg_status enqueue_solve(const DevArena &A, const WeightView &W, const Ins
     a.frozen = L.frozen;
     a.level = L.level;
     a.cur_level = L.cur_level;
+    a.tiles = L.tiles;
+    a.ntiles = L.ntiles;
     a.seed_bits = nullptr;
     const bool first = !L.level || L.cur_level == 0;  // an SCC-ordered solve seeds once, at level 0
     if (first && (L.warm_start || L.preseeded)) {
@@ -1519,9 +1542,13 @@ __global__ void k_widen(const int *in, long long *out, int n) {
 // credits of active instances count: the others were not computed by the
 // launch just run.
 template <typename T>
-__global__ void k_mark_finite(const T *f, int n, unsigned *bits, InstTable I) {
+__global__ void k_mark_finite(const T *f, int n, unsigned *bits, InstTable I, const int *tiles, long long ntiles) {
     const int lane = lane_id();
-    for (int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < n; base += gridDim.x * blockDim.x) {
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const long long nt = tile_count(tiles, ntiles, 0, n);
+    for (long long t = gw; t < nt; t += nw) {
+        const int base = tile_base(tiles, t, 0);
         const int g = base + lane;
         bool fin = g < n && f[g] != Cred<T>::TOP;
         if (fin && I.active) fin = __ldg(I.active + inst_of(I, g)) != 0;
@@ -1558,10 +1585,13 @@ __global__ void k_count_undecided(const T *f, const unsigned *w1, int n, unsigne
 // whose credits all belong to one instance adds them with one atomic).
 template <typename T>
 __global__ void k_count_undecided_inst(const T *f, const unsigned *w1, InstTable I, int nf,
-                                       unsigned long long *count) {
+                                       unsigned long long *count, const int *tiles, long long ntiles) {
     const int lane = lane_id();
-    for (int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < nf; base += gridDim.x * blockDim.x) {
-        const int g = base + lane;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const long long nt = tile_count(tiles, ntiles, 0, nf);
+    for (long long t = gw; t < nt; t += nw) {
+        const int g = tile_base(tiles, t, 0) + lane;
         int i = -1;
         unsigned long long und = 0;
         if (g < nf) {
@@ -1861,8 +1891,8 @@ static eg_status certify(eg_arena *ar, SolveMem &m, long long scale, long long s
         // the warm start's own finds are proven losses too
         k_or_bits<<<(int)std::min<size_t>((words + 255) / 256, 1024), 256, 0, s>>>(m.cert_w1, sc.d.seed_bits,
                                                                                    (int)words);
-        if (cw == 32) k_mark_finite<int><<<wblocks, 256, 0, s>>>((const int *)sc.d.f, (int)n, m.cert_w0, all);
-        else k_mark_finite<long long><<<wblocks, 256, 0, s>>>((const long long *)sc.d.f, (int)n, m.cert_w0, all);
+        if (cw == 32) k_mark_finite<int><<<wblocks, 256, 0, s>>>((const int *)sc.d.f, (int)n, m.cert_w0, all, nullptr, 0);
+        else k_mark_finite<long long><<<wblocks, 256, 0, s>>>((const long long *)sc.d.f, (int)n, m.cert_w0, all, nullptr, 0);
         EG_CUDA_TRY(cudaGetLastError());
         // an exact capped fixpoint computed in int32 goes to the solve's own
         // state, where the output and an in-place caller find it
@@ -1891,8 +1921,8 @@ static eg_status certify(eg_arena *ar, SolveMem &m, long long scale, long long s
         rc = narrow_d ? run_phase<int>(ar, m, sdd, Wd, Ld, s, t, EG_PHASE_DUAL, dev)
                       : run_phase<long long>(ar, m, sdd, Wd, Ld, s, t, EG_PHASE_DUAL, dev);
         if (rc != EG_OK || dev != DEV_OK) return rc;
-        if (narrow_d) k_mark_finite<int><<<wblocks, 256, 0, s>>>((const int *)sdd.d.f, (int)n, m.cert_w1, all);
-        else k_mark_finite<long long><<<wblocks, 256, 0, s>>>((const long long *)sdd.d.f, (int)n, m.cert_w1, all);
+        if (narrow_d) k_mark_finite<int><<<wblocks, 256, 0, s>>>((const int *)sdd.d.f, (int)n, m.cert_w1, all, nullptr, 0);
+        else k_mark_finite<long long><<<wblocks, 256, 0, s>>>((const long long *)sdd.d.f, (int)n, m.cert_w1, all, nullptr, 0);
         EG_CUDA_TRY(cudaGetLastError());
         if ((rc = count(sc.d.f, cw)) != EG_OK) return rc;
         if (h[0] == 0) return finish();
@@ -2114,6 +2144,7 @@ struct eg_plan_impl {
     std::vector<long long> scale, shift, C;
     void *table = nullptr;  // device instance table
     int *lut = nullptr;     // device block lookup of the instance table (non-uniform instances)
+    int *d_tiles = nullptr;  // tile list of the certified trials' launches (allocated on first use)
     InstTable I{};
     StateBuffers sb;
     cudaStream_t own = nullptr;
@@ -2146,6 +2177,7 @@ eg_status plan_release(eg_plan_impl *p) {
     if (p->cert_block) cudaFree(p->cert_block);
     if (p->table) cudaFree(p->table);
     if (p->lut) cudaFree(p->lut);
+    if (p->d_tiles) cudaFree(p->d_tiles);
     if (p->own) cudaStreamDestroy(p->own);
     if (p->ev0) cudaEventDestroy(p->ev0);
     if (p->ev1) cudaEventDestroy(p->ev1);
@@ -2421,7 +2453,36 @@ static eg_status plan_certify(eg_plan_impl *p, cudaStream_t s, long long max_rou
     It.shift = p->d_h2;
     It.C = p->d_C2;
     It.active = p->d_active;
+    // the tiles covering the instances of the set uploaded last (see
+    // tile_count), when they hold under half of the credits; else every tile
+    std::vector<int> htiles;
+    const int *cur_tiles = nullptr;
+    long long cur_ntiles = 0;
+    auto select_tiles = [&](const std::vector<int> &a) -> eg_status {
+        long long sel = 0;
+        for (int i = 0; i < cnt; ++i)
+            if (a[i]) sel += p->n_of[i];
+        cur_tiles = nullptr;
+        cur_ntiles = 0;
+        if (2 * sel >= nf) return EG_OK;
+        htiles.clear();
+        for (int i = 0; i < cnt; ++i) {
+            if (!a[i] || p->n_of[i] == 0) continue;
+            int t0 = p->fbase[i] >> 5;
+            const int t1 = (p->fbase[i + 1] - 1) >> 5;
+            if (!htiles.empty() && htiles.back() >= t0) t0 = htiles.back() + 1;
+            for (int t = t0; t <= t1; ++t) htiles.push_back(t);
+        }
+        if (!p->d_tiles) EG_CUDA_TRY(cudaMalloc((void **)&p->d_tiles, ((size_t)(nf + 31) / 32 + 1) * 4));
+        if (!htiles.empty())
+            EG_CUDA_TRY(cudaMemcpyAsync(p->d_tiles, htiles.data(), htiles.size() * 4, cudaMemcpyHostToDevice, s));
+        cur_tiles = p->d_tiles;
+        cur_ntiles = (long long)htiles.size();
+        return EG_OK;
+    };
     auto upload = [&](const std::vector<int> &a) -> eg_status {
+        eg_status trc = select_tiles(a);
+        if (trc != EG_OK) return trc;
         EG_CUDA_TRY(cudaMemcpyAsync(p->d_s2, hs.data(), (size_t)cnt * 8, cudaMemcpyHostToDevice, s));
         EG_CUDA_TRY(cudaMemcpyAsync(p->d_h2, hh.data(), (size_t)cnt * 8, cudaMemcpyHostToDevice, s));
         EG_CUDA_TRY(cudaMemcpyAsync(p->d_C2, hC.data(), (size_t)cnt * 8, cudaMemcpyHostToDevice, s));
@@ -2433,7 +2494,7 @@ static eg_status plan_certify(eg_plan_impl *p, cudaStream_t s, long long max_rou
     auto count = [&]() -> eg_status {
         EG_CUDA_TRY(cudaMemsetAsync(p->d_cnt, 0, (size_t)cnt * 8, s));
         k_count_undecided_inst<T><<<wblocks_of(nf, sms), 256, 0, s>>>((const T *)p->sb.d.f, p->cert_w1, p->I,
-                                                                      (int)nf, p->d_cnt);
+                                                                      (int)nf, p->d_cnt, cur_tiles, cur_ntiles);
         EG_CUDA_TRY(cudaGetLastError());
         EG_CUDA_TRY(cudaMemcpyAsync(und.data(), p->d_cnt, (size_t)cnt * 8, cudaMemcpyDeviceToHost, s));
         EG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -2460,11 +2521,14 @@ static eg_status plan_certify(eg_plan_impl *p, cudaStream_t s, long long max_rou
         EG_CUDA_TRY(cudaMemcpyAsync(p->sb.d.seed_bits, p->cert_w1, words * 4, cudaMemcpyDeviceToDevice, s));
         Launch Lp = launch_of(ar, 1, max_rounds);
         Lp.preseeded = true;
+        Lp.tiles = cur_tiles;
+        Lp.ntiles = cur_ntiles;
         rc = plan_phase<T>(p, p->sb, It, Lp, s, t, EG_PHASE_CAPPED, dev);
         if (rc != EG_OK || dev != DEV_OK) return rc;
         k_or_bits<<<(int)std::min<size_t>((words + 255) / 256, 1024), 256, 0, s>>>(p->cert_w1, p->sb.d.seed_bits,
                                                                                    (int)words);
-        k_mark_finite<T><<<wblocks, 256, 0, s>>>((const T *)p->sb.d.f, (int)nf, p->cert_w0, It);
+        k_mark_finite<T><<<wblocks, 256, 0, s>>>((const T *)p->sb.d.f, (int)nf, p->cert_w0, It, cur_tiles,
+                                                 cur_ntiles);
         EG_CUDA_TRY(cudaGetLastError());
         if ((rc = count()) != EG_OK) return rc;
         int ndual = 0;
@@ -2492,9 +2556,12 @@ static eg_status plan_certify(eg_plan_impl *p, cudaStream_t s, long long max_rou
             Ld.inv = 1;
             Ld.preseeded = true;
             Ld.frozen = p->cert_w1;
+            Ld.tiles = cur_tiles;
+            Ld.ntiles = cur_ntiles;
             rc = plan_phase<long long>(p, p->sd, It, Ld, s, t, EG_PHASE_DUAL, dev);
             if (rc != EG_OK || dev != DEV_OK) return rc;
-            k_mark_finite<long long><<<wblocks, 256, 0, s>>>((const long long *)p->sd.d.f, (int)nf, p->cert_w1, It);
+            k_mark_finite<long long><<<wblocks, 256, 0, s>>>((const long long *)p->sd.d.f, (int)nf, p->cert_w1, It,
+                                                             cur_tiles, cur_ntiles);
             EG_CUDA_TRY(cudaGetLastError());
             if ((rc = count()) != EG_OK) return rc;
             for (int i = 0; i < cnt; ++i)
@@ -2525,6 +2592,8 @@ static eg_status plan_certify(eg_plan_impl *p, cudaStream_t s, long long max_rou
     EG_CUDA_TRY(cudaMemcpyAsync(p->sb.d.seed_bits, p->cert_w1, words * 4, cudaMemcpyDeviceToDevice, s));
     Launch Lf = launch_of(ar, 1, max_rounds);
     Lf.preseeded = true;
+    Lf.tiles = cur_tiles;
+    Lf.ntiles = cur_ntiles;
     return plan_phase<T>(p, p->sb, It, Lf, s, t, EG_PHASE_FINAL, dev);
 }
 
@@ -2771,6 +2840,8 @@ static Args<long long> resident_args(const Resident &R) {
     a.wait_ns = BARRIER_LIMIT_NS;
     a.level = nullptr;
     a.cur_level = 0;
+    a.tiles = nullptr;
+    a.ntiles = 0;
     return a;
 }
 
