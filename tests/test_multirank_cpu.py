@@ -57,3 +57,26 @@ def test_reference_arm_non_zero_ranks_exit_quietly(capsys):
 
     bench.run_reference(A, 2, 1)  # rank 1 does no work and prints nothing
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_rank0_prints_the_contract_line(capsys, monkeypatch):
+    import json
+
+    import bench
+    import oracle
+
+    oracle.build()
+    monkeypatch.setattr(bench, "SAMPLE_SIDE", 40)  # a small sample of the same generator
+
+    class A:
+        steps, warmup, gpus = 2, 1, 1
+
+    bench.run_reference(A, 1, 0)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["steps"] == 2 and line["warmup"] == 1 and line["higher_is_better"] is True
+    assert line["value"] > 0 and line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert "40x40" in line["cpu_baseline"]["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
