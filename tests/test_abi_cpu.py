@@ -99,3 +99,18 @@ def test_struct_layout_matches_header(tmp_path, struct):
     assert int(got["size"]) == ctypes.sizeof(struct)
     for f in fields:
         assert int(got[f]) == getattr(struct, f).offset, f
+
+
+def test_binding_constants_match_header():
+    # every EG_* integer macro of the header has the same value in the binding
+    # and the other way round (options, phases, statuses, server options)
+    defined = {}
+    for h in HEADERS:
+        for mt in re.finditer(r"^#define\s+(EG_[A-Z0-9_]+)\s+\(?(-?\d+)\)?\s*(?:/\*.*)?$", open(h).read(), flags=re.M):
+            defined[mt.group(1)] = int(mt.group(2))
+    assert {"EG_OPT_SWEEPS", "EG_OPT_CHUNK_EDGES", "EG_OPT_KICK_ROUNDS", "EG_PHASE_LEVEL"} <= set(defined)
+    for name, value in defined.items():
+        if hasattr(eg, name):
+            assert getattr(eg, name) == value, name
+    opts = {n for n in defined if n.startswith("EG_OPT_")}
+    assert opts == {n for n in dir(eg) if n.startswith("EG_OPT_")}
