@@ -455,3 +455,80 @@ def test_cycle_bound_catches_a_wrong_bound():
             if any(exact[v] != TOP64 for v in verts):
                 broke += 1
     assert broke > 0
+
+
+# Reading 24 (dense sweeps).  A model of the solver's sweeps and of the
+# worklist rounds that follow them: each sweep raises every credit, in a random
+# order, to its lift (min over edges for player 0, max for player 1), reading
+# each successor either as it is now or as it was when the sweep began (what a
+# concurrent sweep may see); the rounds then start from the credits the last
+# sweep raised.  The credits must stay at or below the least fixpoint after
+# every sweep and end exactly at it.
+
+def _ominus(x, wt, C):
+    if x == TOP64:
+        return TOP64
+    d = x - wt
+    return TOP64 if d > C else max(0, d)
+
+
+def _sweep_model(a, C, sweeps, rng, exact, frontier=True):
+    rp = np.asarray(a.row_ptr)
+    col = np.asarray(a.col)
+    w = np.asarray(a.w, dtype=np.int64)
+    p1 = gen.unpack_owner(a.owner_bits, a.n)
+    preds = [[] for _ in range(a.n)]
+    for v in range(a.n):
+        for k in range(rp[v], rp[v + 1]):
+            preds[int(col[k])].append((v, k))
+
+    def lift(v, read):
+        vals = [_ominus(read(int(col[k])), int(w[k]), C) for k in range(rp[v], rp[v + 1])]
+        return max(vals) if p1[v] else min(vals)
+
+    f = [lift(v, lambda u: 0) for v in range(a.n)]  # the init: the lift over f = 0
+    last = set()
+    for _ in range(sweeps):
+        snap = list(f)
+        last = set()
+        for v in rng.permutation(a.n):
+            v = int(v)
+            t = lift(v, lambda u: snap[u] if rng.random() < 0.5 else f[u])
+            if t > f[v]:
+                f[v] = t
+                last.add(v)
+        assert all(x <= e for x, e in zip(f, exact))
+    from collections import deque
+
+    queue = deque(sorted(last) if frontier else [])
+    queued = set(queue)
+    while queue:  # the rounds: rises pushed to predecessors
+        u = queue.popleft()
+        queued.discard(u)
+        for p, k in preds[u]:
+            t = _ominus(f[u], int(w[k]), C)
+            if t <= f[p]:
+                continue
+            nv = t if p1[p] else lift(p, lambda x: f[x])
+            if nv > f[p]:
+                f[p] = nv
+                if p not in queued:
+                    queue.append(p)
+                    queued.add(p)
+    return np.asarray(f, dtype=np.int64)
+
+
+def test_sweeps_then_frontier_reach_the_least_fixpoint():
+    rng = np.random.default_rng(24)
+    games = [_tiny(seed) for seed in range(300)]
+    games += [gen.varied_game(int(n), 1, 4, 12, seed=500 + i) for i, n in enumerate(rng.integers(20, 80, 40))]
+    short = 0
+    for a in games:
+        exact = oracle.brute_force(a.n, a.row_ptr, a.col, a.w, a.owner_bits) if a.n <= 7 else solve(a)[0]
+        C = oracle.bound(a.n, a.row_ptr, a.w)
+        for sweeps in (1, 2, 4):
+            np.testing.assert_array_equal(_sweep_model(a, C, sweeps, rng, exact), exact)
+            # without the last sweep's frontier the rounds miss rises
+            if not np.array_equal(_sweep_model(a, C, sweeps, rng, exact, frontier=False), exact):
+                short += 1
+    assert short > 0
